@@ -1,0 +1,295 @@
+"""Pins of the oracle's dynamics against conservation laws, limits and closed forms.
+
+Every test here runs the C oracle (FP64) and compares it with something the
+paper or the mathematics fixes: exact per-colour mass conservation, momentum
+balance, the BGK limit (an independent numpy transcription), the viscosity of
+Eq. (shear) from shear-wave decay, the sound speed of Eq. (press), steady
+Poiseuille flow between halfway bounce-back walls, Laplace's law with
+Eq. (sigma) and the Lamb / Miller-Scriven oscillation period.
+"""
+import numpy as np
+import pytest
+
+import lbm_inputs as L
+import oracle
+from tests import bgk_reference as bgk
+
+C = oracle.tables()[0]
+
+
+def _run(work, steps, u_amp=0.0, seed=0, **over):
+    w = {**work, "params": {**work["params"], **over}}
+    rr, rb, u = L.initial_fields(w, seed=seed, u_amp=u_amp)
+    o = oracle.Oracle(w["shape"], w["params"])
+    o.init_fields(rr, rb, u)
+    m0 = o.f[0].sum(), o.f[1].sum(), np.einsum("id,kizyx->d", C, o.f)
+    o.step(steps)
+    return o, m0
+
+
+def test_colour_mass_conserved_periodic_and_walls():
+    """Per-colour mass is exact: recolouring splits mass in proportion, the perturbation (square
+    restored, App. B conditions) has zero sum, s1 = 0 keeps the conserved moments."""
+    for work in (L.static_droplet(n=12, R=3.5),
+                 L.parity_cases()[1][1]):  # ragged box, no-slip + free-slip faces, gamma = 1.5
+        o, m0 = _run(work, 40, u_amp=0.02, seed=3)
+        assert abs(o.f[0].sum() - m0[0]) < 1e-12 * m0[0]
+        assert abs(o.f[1].sum() - m0[1]) < 1e-12 * m0[1]
+
+
+def test_planted_unsquared_perturbation_breaks_mass():
+    """The perturbation exactly as printed (no square, reading R1) injects mass; the pin above catches it."""
+    o, m0 = _run(L.static_droplet(n=12, R=3.5), 20, perturb_literal=1)
+    drift = abs(o.f[0].sum() + o.f[1].sum() - m0[0] - m0[1])
+    assert drift > 1e-6
+
+
+def test_momentum_conserved_without_force():
+    o, m0 = _run(L.static_droplet(n=12, R=3.5, rho_r0=1.5), 30, u_amp=0.02, seed=4)
+    j = np.einsum("id,kizyx->d", C, o.f)
+    np.testing.assert_allclose(j, m0[2], atol=1e-11)
+
+
+def test_uniform_force_momentum_gain():
+    """Eqs. (Momentum), (ketF)-(ketFd): a uniform force density F adds exactly F per node per step."""
+    g = (1e-5, -2e-5, 3e-5)
+    work = L.static_droplet(n=10, R=3.0, rho_r0=1.5)
+    steps = 25
+    o, m0 = _run(work, steps, force_mode=3, g=g)
+    j = np.einsum("id,kizyx->d", C, o.f)
+    np.testing.assert_allclose(j - m0[2], np.array(g) * o.N * steps, rtol=1e-9, atol=1e-13)
+
+
+def _bgk_case():
+    p = dict(rho_r0=1.4, rho_b0=1.0, nu_r=0.04, nu_b=0.04, A=0.01, beta=0.7, g=(0.0, 0.0, -1e-4),
+             force_mode=1, bc=(0,) * 6, seed=0)
+    s = 1.0 / (3 * 0.04 + 0.5)
+    p["s"] = L.uniform_rates(s)
+    work = dict(name="bgk", shape=(6, 5, 7), params=p, fields=("random_blobs", dict(seed=2, blobs=2)))
+    return work, s
+
+
+def test_bgk_limit_matches_independent_transcription():
+    """All MRT rates equal (K = s I on non-conserved moments) == the single-relaxation-time form."""
+    work, s = _bgk_case()
+    rr, rb, u = L.initial_fields(work, seed=9, u_amp=0.03)
+    o = oracle.Oracle(work["shape"], work["params"])
+    o.init_fields(rr, rb, u)
+    perm = bgk.to_paper_order(C)
+    fr = np.empty_like(o.f[0])
+    fb = np.empty_like(o.f[1])
+    fr[perm] = o.f[0]
+    fb[perm] = o.f[1]
+    for _ in range(4):
+        o.step(1)
+        fr, fb = bgk.step(fr, fb, work["params"], s)
+        np.testing.assert_allclose(o.f[0], fr[perm], rtol=0, atol=1e-13)
+        np.testing.assert_allclose(o.f[1], fb[perm], rtol=0, atol=1e-13)
+
+
+def test_mrt_differs_from_bgk_when_rates_differ():
+    """Guard for the pin above: with Suga's rates the two operators must not coincide."""
+    work, s = _bgk_case()
+    work["params"]["s"] = L.suga_rates()
+    rr, rb, u = L.initial_fields(work, seed=9, u_amp=0.03)
+    o = oracle.Oracle(work["shape"], work["params"])
+    o.init_fields(rr, rb, u)
+    perm = bgk.to_paper_order(C)
+    fr, fb = np.empty_like(o.f[0]), np.empty_like(o.f[1])
+    fr[perm], fb[perm] = o.f[0], o.f[1]
+    o.step(1)
+    fr, fb = bgk.step(fr, fb, work["params"], s)
+    assert np.abs(o.f[0] - fr[perm]).max() > 1e-6
+
+
+@pytest.mark.parametrize("nu", [0.01, 0.05])
+def test_shear_wave_viscosity(nu):
+    """Eq. (shear): a shear wave u_x(y) decays as exp(-nu k^2 t) with nu = (1/s6 - 1/2)/3."""
+    n = 32
+    p = dict(rho_r0=1.0, rho_b0=1.0, nu_r=nu, nu_b=nu, A=0.0, beta=0.7, s=L.suga_rates(), bc=(0,) * 6)
+    shape = (4, n, 4)
+    o = oracle.Oracle(shape, p)
+    z, y, x = np.meshgrid(np.arange(4), np.arange(n), np.arange(4), indexing="ij")
+    k = 2 * np.pi / n
+    u = np.zeros((3, 4, n, 4))
+    u[0] = 1e-4 * np.sin(k * y)
+    o.init_fields(np.ones((4, n, 4)), np.zeros((4, n, 4)), u)
+
+    def amp():
+        _, _, uu = o.macro()
+        return 2 * np.mean(uu[0] * np.sin(k * y))
+
+    o.step(50)
+    a0 = amp()
+    steps = 400
+    o.step(steps)
+    a1 = amp()
+    nu_meas = -np.log(a1 / a0) / (k * k * steps)
+    assert nu_meas == pytest.approx(nu, rel=0.01)
+
+
+def test_sound_speed_of_enhanced_equilibrium():
+    """Eq. (press): a pure phase with alpha_k has c_s^2 = 9(1 - alpha_k)/19 (gamma = 2 -> 1/6)."""
+    n = 48
+    p = dict(rho_r0=2.0, rho_b0=1.0, nu_r=0.01, nu_b=0.01, A=0.0, beta=0.7, s=L.suga_rates(), bc=(0,) * 6)
+    ar = oracle.alpha_r(p)
+    cs2 = 9 * (1 - ar) / 19
+    shape = (n, 2, 2)
+    o = oracle.Oracle(shape, p)
+    x = np.arange(n)[None, None, :] * np.ones((2, 2, 1))
+    k = 2 * np.pi / n
+    o.init_fields(2.0 * (1 + 1e-4 * np.cos(k * x)), np.zeros((2, 2, n)))
+    series = []
+    for _ in range(300):
+        o.step(1)
+        r, _, _ = o.macro()
+        series.append(np.mean((r - 2.0) * np.cos(k * x)))
+    s = np.array(series)
+    # standing wave: cos(omega t); omega from the first zero crossings
+    zc = np.where(np.sign(s[:-1]) != np.sign(s[1:]))[0]
+    t0 = zc[0] + s[zc[0]] / (s[zc[0]] - s[zc[0] + 1])
+    t1 = zc[1] + s[zc[1]] / (s[zc[1]] - s[zc[1] + 1])
+    half_period = t1 - t0
+    cs_meas = np.pi / half_period / k
+    assert cs_meas ** 2 == pytest.approx(cs2, rel=0.01)
+
+
+def _poiseuille(nu, rates, H=12, Fx=1e-6, steps=3000):
+    p = dict(rho_r0=1.0, rho_b0=1.0, nu_r=nu, nu_b=nu, A=0.0, beta=0.7, s=rates, g=(Fx, 0.0, 0.0),
+             force_mode=3, bc=(0, 0, 0, 0, 1, 1))
+    o = oracle.Oracle((3, 3, H), p)
+    o.init_fields(np.ones((H, 3, 3)), np.zeros((H, 3, 3)))
+    o.step(steps)
+    _, _, u = o.macro()
+    z = np.arange(H)
+    return u[0, :, 1, 1], Fx / (2 * nu) * (z + 0.5) * (H - 0.5 - z)
+
+
+def test_poiseuille_between_bounce_back_walls():
+    """Halfway bounce-back + forcing: steady u_x(z) = F/(2 rho nu) (z+1/2)(H-1/2-z).
+
+    With one relaxation rate at tau = 1/2 + sqrt(3)/4 (the two-relaxation-time parameter 3/16)
+    halfway bounce-back puts the wall exactly half-way, so the profile is exact; with Suga's
+    rates the known rate-dependent wall slip remains (5 % at the wall nodes)."""
+    tau = 0.5 + np.sqrt(3) / 4
+    nu = (tau - 0.5) / 3
+    got, want = _poiseuille(nu, L.uniform_rates(1 / tau))
+    np.testing.assert_allclose(got, want, rtol=1e-6)
+    got, want = _poiseuille(0.1, L.suga_rates())
+    np.testing.assert_allclose(got, want, rtol=5e-2)
+
+
+def test_free_slip_walls_keep_plug_flow():
+    """Specular reflection: a uniform force parallel to free-slip walls gives uniform acceleration."""
+    p = dict(rho_r0=1.0, rho_b0=1.0, nu_r=0.05, nu_b=0.05, A=0.0, beta=0.7, s=L.suga_rates(), g=(1e-5, 0.0, 0.0),
+             force_mode=3, bc=(0, 0, 2, 2, 2, 2))
+    o = oracle.Oracle((3, 6, 7), p)
+    o.init_fields(np.ones((7, 6, 3)), np.zeros((7, 6, 3)))
+    o.step(200)
+    _, _, u = o.macro()
+    np.testing.assert_allclose(u[0], 1e-5 * 200.5, rtol=1e-9)  # momentum 200 F plus the F/2 shift
+    assert np.abs(u[1:]).max() < 1e-14
+
+
+def test_suga_rates_unstable_at_tau_one():
+    """Reading for the tau = 1 static droplet: the printed M with Suga's rates amplifies a mode at
+    rest (|lambda| > 1) for s6 = 1 but not for s6 >= 1.8, the range of the paper's own cases."""
+    _, M, Mi, w, _, ks = oracle.tables()
+    J = np.array([[w[i] * (1 + 3 * C[i] @ C[j]) for j in range(27)] for i in range(27)])
+    suga = L.suga_rates()
+
+    def worst(s6):
+        K = np.array([s6 if k in (6, 8) else suga[j] for j, k in enumerate(ks)])
+        A = np.eye(27) - Mi @ np.diag(K) @ M @ (np.eye(27) - J)
+        best = 0.0
+        for kk in np.linspace(0, np.pi, 9):
+            S = np.diag(np.exp(-1j * (C @ np.array([kk, kk, kk]))))
+            best = max(best, np.abs(np.linalg.eigvals(S @ A)).max())
+        return best
+
+    assert worst(1.0) > 1.05
+    assert worst(1.85) < 1 + 1e-9
+
+
+def _laplace(o, work):
+    r, b, _ = o.macro()
+    p = work["params"]
+    ar, ab = oracle.alpha_r(p), 8 / 27
+    phi = (r - b) / (r + b)
+    pr = r * 9 * (1 - ar) / 19 + b * 9 * (1 - ab) / 19
+    dp = pr[phi > 0.99].mean() - pr[phi < -0.99].mean()
+    Req = (3 * ((1 + phi) / 2).sum() / (4 * np.pi)) ** (1 / 3)
+    return dp, Req
+
+
+@pytest.mark.slow
+def test_laplace_law_static_droplet():
+    """Eq. (lap) with Eq. (sigma): sigma = (4/9) A tau, tau = 3 nu + 1/2 (reading R2).
+
+    32^3 periodic box, R = 8, W = 4, tau = 1 (unit rates for the other moments, reading for the
+    tau = 1 case), 1000 steps.  The paper's error is 1.6 % at R = 20 and grows roughly as 1/R^2;
+    at R = 8 we require 10 %.  Halving A must halve dp to 3 %.
+    """
+    work = L.static_droplet()
+    work["params"]["s"] = L.uniform_rates(1.0)
+    res = {}
+    for A in (0.01, 0.005):
+        o, _ = _run(work, 1000, A=A)
+        dp, Req = _laplace(o, work)
+        sigma_th = 4 / 9 * A * (3 * work["params"]["nu_r"] + 0.5)
+        res[A] = (dp, abs(dp * Req / 2 - sigma_th) / sigma_th)
+    assert res[0.01][1] < 0.10
+    assert res[0.005][1] < 0.10
+    assert res[0.01][0] / res[0.005][0] == pytest.approx(2.0, rel=0.03)
+
+
+def _lamb_period(R, sigma, rho1, rho2, nu):
+    """Eqs. (resoFreq), (Lamb): second-mode period of Miller & Scriven for a drop of radius R."""
+    n = 2
+    mu1, mu2 = rho1 * nu, rho2 * nu
+    w0 = np.sqrt(n * (n + 1) * (n - 1) * (n + 2) * sigma / (R ** 3 * (n * rho2 + (n + 1) * rho1)))
+    chi = ((2 * n + 1) ** 2 * np.sqrt(mu1 * mu2 * rho1 * rho2) /
+           (np.sqrt(2) * R * (n * rho2 + (n + 1) * rho1) * (np.sqrt(mu1 * rho1) + np.sqrt(mu2 * rho2))))
+    w = w0 - 0.5 * chi * np.sqrt(w0) + 0.25 * chi ** 2
+    return 2 * np.pi / w
+
+
+def _half_period(A, steps):
+    n, axes, nu = 32, (10.0, 8.0, 8.0), 0.01
+    work = L.oscillating_droplet(n=n, axes=axes, nu=nu, A=A)
+    rr, rb, u = L.initial_fields(work)
+    o = oracle.Oracle(work["shape"], work["params"])
+    o.init_fields(rr, rb, u)
+    c = 0.5 * (n - 1)
+    ts, xs = [], []
+    for _ in range(steps // 10):
+        o.step(10)
+        r, b, _ = o.macro()
+        line = ((r - b) / (r + b))[15:17, 15:17, :].mean(axis=(0, 1))
+        j = np.where((line[:-1] > 0) & (line[1:] <= 0))[0][-1]
+        xs.append(j + line[j] / (line[j] - line[j + 1]) - c)
+        ts.append(o.t)
+    xs, ts = np.array(xs), np.array(ts)
+    i_max = int(np.argmax(xs[:20]))
+    i_min = i_max + int(np.argmin(xs[i_max:]))
+    assert 0 < i_min < len(xs) - 3, "no minimum of the major semi-axis inside the run"
+
+    def vertex(i):  # parabolic refinement of an extremum
+        y0, y1, y2 = xs[i - 1], xs[i], xs[i + 1]
+        return ts[i] + 10 * 0.5 * (y0 - y2) / (y0 - 2 * y1 + y2)
+
+    sigma = 4 / 9 * A * (3 * nu + 0.5)
+    return vertex(i_min) - vertex(max(i_max, 1)), _lamb_period((10 * 8 * 8) ** (1 / 3), sigma, 1.0, 1.0, nu)
+
+
+@pytest.mark.slow
+def test_oscillating_droplet_period():
+    """Eqs. (resoFreq)-(Lamb): the n = 2 period of a slightly prolate drop (32^3, axes 10/8/8,
+    nu = 0.01, gamma = 1).  At this small radius (R_e = 8.6, interface width 4 ~ R/2, periodic
+    box 32) the measured period runs 12-17 % long, so we require 20 % on the period and 5 % on
+    the ratio of the periods at A and A/2, which cancels most of the finite-size error."""
+    h1, T1 = _half_period(0.01, 1300)
+    h2, T2 = _half_period(0.005, 1700)
+    assert abs(2 * h1 - T1) / T1 < 0.20
+    assert abs(2 * h2 - T2) / T2 < 0.20
+    assert (h2 / h1) == pytest.approx(T2 / T1, rel=0.05)
