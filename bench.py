@@ -1,0 +1,407 @@
+"""Benchmark of the D3Q27 colour-fluid update on GB300 (one JSON line on rank 0).
+
+Workload: the liquid-jet set-up of Sec. IV.A at 128 x 128 x 512 nodes (nozzle
+D = 16 in the z = 0 wall, Re = 3.4e3, gamma = 1.2, eta = 3, A = 0.005,
+1 % seeded inlet noise, convective outflow on top), synthetic: the box starts
+filled with the continuous phase at rest, as in the paper.
+
+One bench step = one time step of the whole hot path (density pass, fused
+collide-perturb-recolour-stream pass, outflow pass) over the whole box.
+`value` is MLUPS (million lattice-node updates per second) with the state
+resident in HBM; the state (0.9 GB in 16-bit storage, 1.8 GB in FP32) is far
+larger than the 129 MB L2, so every step streams it from HBM.
+
+Also reported: the same metric for FP32 storage, the leading-edge and mass
+differences between the two storages after the timed steps (the "stated
+error"), the live roofline of the dominant kernel (CUDA events on its
+stream), an end-to-end number through the C ABI with host buffers, the FP64
+CPU oracle on a bounded sample of the workload on the host cores, and the SM
+clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--storage f16|bf16|f32]
+  python bench.py --impl reference ...   (the FP64 CPU oracle, the reference arm)
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import lbm_inputs as L  # noqa: E402
+
+METRIC = "D3Q27 color-fluid MLUPS & % HBM roofline, mixed vs FP32 at stated error"
+UNIT = "MLUPS"
+# algorithmic bytes per node and step of each kernel:
+#   density pass: read 54 populations, write (rho, phi)
+#   collide-stream pass: read (rho, phi) once, read and write 54 populations
+POP_BYTES = {"f64": 8 * 54, "f32": 4 * 54, "f16": 4 * 27, "bf16": 4 * 27}
+DENS_BYTES = {"f64": 16, "f32": 8, "f16": 8, "bf16": 8}
+
+
+def workload(seed=1234):
+    return L.jet(seed=seed)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1705_03141_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(storage):
+    """DRAM bytes per launch of the collide-stream kernel from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", f"collide_stream_jet_{storage}.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"kernel_sources_sha:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != kernel_hash():
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.f:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, name in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# distributed helpers (torchrun: one process per GPU, independent jets per rank)
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(value, ws, backend_device=None):
+    """Largest value over all ranks (the slowest rank sets the whole-job time)."""
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=backend_device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------
+
+def cpu_oracle_sample(seconds_budget=20.0, nz_sample=32, seed=1234, steps=None):
+    """FP64 CPU oracle on a bounded sample of the jet workload: the bottom nz_sample planes of the
+    box (same nozzle, walls and outflow), started from rest; returns (MLUPS, cores, steps, nodes)."""
+    import oracle
+
+    w = L.jet(nz=nz_sample, seed=seed)
+    rr, rb, u = L.initial_fields(w)
+    o = oracle.Oracle(w["shape"], w["params"])
+    o.init_fields(rr, rb, u)
+    nodes = o.N
+    t0 = time.perf_counter()
+    o.step(1)
+    one = time.perf_counter() - t0
+    if steps is None:
+        steps = max(1, int(seconds_budget / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return nodes * steps / dt / 1e6, oracle.num_threads(), steps, nodes, dt
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, on the host cores, on a bounded sample of
+    the jet workload (its bottom planes, same nozzle, walls and outflow) sized so that warm-up and
+    timed steps take about a minute; one oracle step of the sample per bench step."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    def sample(nz):
+        w = L.jet(nz=nz)
+        rr, rb, u = L.initial_fields(w)
+        o = oracle.Oracle(w["shape"], w["params"])
+        o.init_fields(rr, rb, u)
+        return o
+
+    o = sample(32)
+    t0 = time.perf_counter()
+    o.step(1)
+    per_plane = (time.perf_counter() - t0) / 32
+    nz = int(max(4, min(32, 60.0 / max((args.steps + args.warmup) * per_plane, 1e-9))))
+    o = sample(nz)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    mlups = o.N * args.steps / dt / 1e6
+    desc = (f"jet workload cut to its bottom {nz} planes (128x128x{nz} = {o.N} nodes, same nozzle, walls and "
+            f"outflow), one FP64 oracle step per bench step")
+    line = {"metric": METRIC, "value": mlups, "unit": UNIT, "impl": "reference", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "jet_128x128x512_D16 (sampled)", "nodes": o.N, "storage": "f64 (CPU)"},
+            "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def end_to_end(pkg, torch, w, rr, rb, u, args, ws, dev):
+    """The same metric through the C ABI with host buffers: lbm_init_fields from pinned host
+    fields, the steps, lbm_diag to the host every 200 steps, lbm_macro into pinned host buffers."""
+    shape = w["shape"]
+    N = shape[0] * shape[1] * shape[2]
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    hr, hb, hu = pin(rr), pin(rb), pin(u)
+    out = (torch.empty(rr.shape, dtype=torch.float64).pin_memory(),
+           torch.empty(rb.shape, dtype=torch.float64).pin_memory(),
+           torch.empty(u.shape, dtype=torch.float64).pin_memory())
+    late = pkg.Lattice(shape, w["params"], storage=args.storage)
+    late.init_fields(hr, hb, hu)
+    late.step(args.warmup)
+    late.synchronize()
+    diag_every = 200
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    late.init_fields(hr, hb, hu)
+    done = 0
+    while done < args.steps:
+        k = min(diag_every, args.steps - done)
+        late.step(k)
+        done += k
+        late.diag()  # device -> host read of the step's diagnostics (masses, leading edge, dp)
+    late.macro(out)
+    torch.cuda.synchronize()
+    e2e_dt = max_over_ranks(time.perf_counter() - t0, ws, dev)
+    late.close()
+    n_diag = (args.steps + diag_every - 1) // diag_every
+    h2d = 5 * N * 8
+    d2h = 5 * N * 8 + n_diag * 7 * 8
+
+    return {"value": ws * N * args.steps / e2e_dt / 1e6, "unit": UNIT,
+            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+            "what": "lbm_init_fields from pinned host fields, the steps, lbm_diag to host every "
+                    f"{diag_every} steps, lbm_macro to pinned host buffers at the end"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f16", choices=["f16", "bf16", "f32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import paper_1705_03141_gb300 as pkg
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pkg.library()
+
+    # each rank runs its own jet (independent seed): weak scaling, no data-path collective
+    w = workload(seed=1234 + rank)
+    shape = w["shape"]
+    N = shape[0] * shape[1] * shape[2]
+    rr, rb, u = L.initial_fields(w)
+
+    def make(storage):
+        lat = pkg.Lattice(shape, w["params"], storage=storage)
+        lat.init_fields(rr, rb, u)
+        return lat
+
+    def timed(lat, steps):
+        """device time of `steps` steps (CUDA events on the lattice's stream, barrier + sync around)."""
+        barrier(ws)
+        torch.cuda.synchronize()
+        s = lat.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        lat.step(steps)
+        e1.record(s)
+        torch.cuda.synchronize()
+        barrier(ws)
+        return e0.elapsed_time(e1) / 1e3
+
+    # ---- headline: packed 16-bit storage ---------------------------------
+    lat = make(args.storage)
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        dt = timed(lat, args.steps)
+    dt_max = max_over_ranks(dt, ws, dev)
+    mlups = ws * N * args.steps / dt_max / 1e6
+    kps = lat.kernels_per_step
+    diag_h = lat.diag()
+    # live per-kernel timing of the same configuration (CUDA events on the kernels' stream)
+    ms = lat.profile_step(min(200, args.steps))
+    lat.close()
+
+    # ---- FP32 storage, same workload and steps (the "vs FP32" comparison) ----
+    fp32 = None
+    if not args.no_fp32:
+        lat32 = make("f32")
+        lat32.step(args.warmup)
+        dt32 = max_over_ranks(timed(lat32, args.steps), ws, dev)
+        diag32 = lat32.diag()
+        ms32 = lat32.profile_step(min(200, args.steps))
+        lat32.close()
+        D = w["params"]["inflow"]["D"]
+        bytes32 = N * (POP_BYTES["f32"] * 2 + DENS_BYTES["f32"])
+        fp32 = {"value": ws * N * args.steps / dt32 / 1e6, "ms_per_step": dt32 / args.steps * 1e3,
+                "collide_ms": ms32[1], "collide_gbs": bytes32 / (ms32[1] * 1e-3) / 1e9,
+                "stated_error": {
+                    "after_steps": args.warmup + args.steps,
+                    "leading_edge_abs_diff_over_D": abs(diag_h["z_le"] - diag32["z_le"]) / D,
+                    "leading_edge_over_D": diag32["z_le"] / D,
+                    "mass_r_rel_diff": abs(diag_h["mass_r"] - diag32["mass_r"]) / max(diag32["mass_r"], 1e-300),
+                    "mass_b_rel_diff": abs(diag_h["mass_b"] - diag32["mass_b"]) / diag32["mass_b"]}}
+
+    # ---- end to end through the C ABI with host buffers ------------------
+    e2e = None if args.no_e2e else end_to_end(pkg, torch, w, rr, rb, u, args, ws, dev)
+
+    # ---- roofline of the dominant kernel ----------------------------------
+    peak, peak_kind = peaks()
+    alg_bytes = N * (POP_BYTES[args.storage] * 2 + DENS_BYTES[args.storage])
+    achieved = alg_bytes / (ms[1] * 1e-3) / 1e9
+    traffic = profiled_traffic(args.storage)
+    roof = {"bound": "hbm", "kernel": "k_collide_stream", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+            "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": ms[1],
+            "density_pass_ms": ms[0], "outflow_ms": ms[2],
+            "step_share_collide": ms[1] / max(sum(ms), 1e-12)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, cores, st, nodes, cdt = cpu_oracle_sample()
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"jet workload cut to its bottom 32 planes ({nodes} nodes), {st} FP64 oracle steps "
+                         f"from rest ({cdt:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": dt_max / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": args.storage,
+                "data": "synthetic",
+                "config": {"workload": w["name"], "nodes_per_gpu": N, "grid": list(shape),
+                           "storage": args.storage, "arithmetic": "f32",
+                           "l2": "state larger than L2 (%.2f GB per GPU), no flush needed" %
+                                 (N * POP_BYTES[args.storage] / 1e9),
+                           "parallelism": f"{ws} independent jets (one per GPU)"},
+                "fp32_storage": fp32,
+                "roofline": roof,
+                "cpu_baseline": cpu,
+                "e2e": e2e,
+                "gpu_launches": kps * args.steps,
+                "clocks": clk.summary(),
+                "kernel_sources_sha": kernel_hash()}
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

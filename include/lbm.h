@@ -1,0 +1,228 @@
+/*
+ * lbm.h -- C ABI of the GB300 D3Q27 colour-fluid lattice Boltzmann library.
+ *
+ * The library advances the two-colour (red r / blue b) lattice Boltzmann model
+ * of Saito, Abe & Koyama (arXiv 1705.03141), Sec. II: D3Q27 velocities
+ * (Eq. velSet), MRT collision with the moment set of Eq. (momentSet) and the
+ * relaxation matrix K, the enhanced equilibrium Eq. (EES) with phi_i^k
+ * (Eq. varphi_ik) and Phi_i^k (Eq. Phi), MRT body forcing Eqs. (ketF)-(ketFd),
+ * the generalised perturbation operator Eq. (perturb), recolouring (Sec. II),
+ * streaming (Eq. LBE) and the jet boundaries of Sec. IV.A (circular
+ * equilibrium inlet, free-slip walls, convective outflow).
+ *
+ * Conventions for every call:
+ *  - Every call returns an lbm_status and never aborts the process.  NULL
+ *    handles or pointers, bad sizes or bad parameters give LBM_EINVAL; the
+ *    text of the last error is available from lbm_last_error().
+ *  - Scalar fields are SoA arrays of N = nx*ny*nz doubles with x fastest:
+ *    idx = x + nx*(y + ny*z).  Vector fields are three such arrays back to
+ *    back (u_x, then u_y, then u_z).
+ *  - Population arrays are [2][27][nz][ny][nx] doubles: colour (0 red,
+ *    1 blue), then the direction i = 1..27 in the paper's order (the order of
+ *    rows 2-4 of the printed M, App. A), then the node.  They hold the
+ *    post-streaming populations f_i^k(x, t) at the handle's current time t.
+ *  - Every buffer a caller passes is caller-owned; the library never frees it
+ *    and never keeps a pointer to it after the call returns.  Such a buffer
+ *    may be host memory or device memory of the handle's device; the library
+ *    detects which.
+ *  - Device work is enqueued on the handle's CUDA stream (lbm_params.cuda_stream,
+ *    or the legacy default stream when NULL).  lbm_step() only enqueues;
+ *    calls that return data (lbm_macro, lbm_diag, lbm_get_populations) and
+ *    lbm_synchronize() wait for that stream.
+ *  - One handle is used by one host thread at a time.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define LBM_EXPORT __attribute__((visibility("default")))
+#else
+#define LBM_EXPORT
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = -1,    /* invalid argument, size or parameter */
+  LBM_ENOMEM = -2,    /* device or host allocation failed, or workspace too small */
+  LBM_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
+  LBM_EUNSTABLE = -4, /* the watchdog saw a non-finite or non-positive density */
+  LBM_ETIMEOUT = -5,  /* reserved for bounded device-side waits */
+  LBM_ESTATE = -6     /* call not valid in the handle's current state */
+} lbm_status;
+
+/* How populations are held in device memory.  All collision arithmetic is
+ * FP32 except in LBM_STORE_F64, which computes in FP64 and is the mode that
+ * matches the FP64 CPU oracle.  LBM_STORE_F16 / LBM_STORE_BF16 keep, per
+ * direction and node, the total population as a deviation from its
+ * rest-state value in half / bfloat16 plus the red fraction f^r/f as an
+ * unsigned 16-bit fixed-point number (4 bytes per direction and node). */
+typedef enum {
+  LBM_STORE_F64 = 0,
+  LBM_STORE_F32 = 1,
+  LBM_STORE_F16 = 2,
+  LBM_STORE_BF16 = 3
+} lbm_storage;
+
+/* Face conditions, faces ordered (-x, +x, -y, +y, -z, +z).
+ *  PERIODIC    both faces of an axis must be periodic.
+ *  NOSLIP      halfway bounce-back (Sec. III.C walls).
+ *  FREESLIP    specular reflection of the wall-normal velocity component
+ *              (Sec. IV.A wall boundary).
+ *  INFLOW_WALL a free-slip wall whose plane carries the circular inlet set by
+ *              lbm_set_inflow(); only allowed on -z.
+ *  OUTFLOW     convective outflow of Sec. IV.A; only allowed on +z.
+ * Gradients next to a non-periodic face use a mirror ghost value (zero
+ * normal gradient). */
+typedef enum {
+  LBM_BC_PERIODIC = 0,
+  LBM_BC_NOSLIP = 1,
+  LBM_BC_FREESLIP = 2,
+  LBM_BC_INFLOW_WALL = 3,
+  LBM_BC_OUTFLOW = 4
+} lbm_bc;
+
+/* Body force F(x, t) used in Eq. (Momentum) and Eq. (ketFd).
+ *  NONE       F = 0.
+ *  BUOYANCY   F = (rho - (rho_r0 + rho_b0)/2) g  (Rayleigh-Taylor, Sec. III.C;
+ *             gravity acts on the density excess over the mean initial density).
+ *  DISPERSED  F = (rho - rho_b0) g  (jet, Eq. bodyForceJet).
+ *  UNIFORM    F = g  (a constant force density). */
+typedef enum {
+  LBM_FORCE_NONE = 0,
+  LBM_FORCE_BUOYANCY = 1,
+  LBM_FORCE_DISPERSED = 2,
+  LBM_FORCE_UNIFORM = 3
+} lbm_force;
+
+typedef struct {
+  double rho_r0, rho_b0; /* initial phase densities; gamma = rho_r0/rho_b0 sets
+                            alpha_r = 1 - (1 - alpha_b)/gamma with alpha_b = 8/27
+                            (Grunau relation and the choice of alpha_b, Sec. II) */
+  double nu_r, nu_b;     /* kinematic viscosities; per node
+                            nu_bar = (1+phi)/2 nu_r + (1-phi)/2 nu_b and
+                            s6 = s8 = 1/(3 nu_bar + 1/2) (Eq. shear) */
+  double A, beta;        /* perturbation strength of Eq. (perturb) (A_r = A_b = A)
+                            and recolouring parameter beta */
+  double s[27];          /* relaxation rate of each moment of Eq. (momentSet), in
+                            moment order; the entries of the s6 and s8 slots
+                            (moments 6-10) are ignored and replaced by the local
+                            shear rate; all rates must lie in [0, 2) */
+  double g[3];           /* gravity / force vector of the force mode */
+  int force_mode;        /* lbm_force */
+  int bc[6];             /* lbm_bc per face (-x,+x,-y,+y,-z,+z) */
+  int storage;           /* lbm_storage */
+  unsigned long long seed; /* seed of the inlet velocity noise */
+  void* cuda_stream;     /* cudaStream_t to enqueue on; NULL = legacy default stream */
+  void* workspace;       /* optional caller-owned device memory for all device
+                            state (populations, density field, buffers); must
+                            hold lbm_workspace_size() bytes, be 256-byte
+                            aligned and outlive the handle.  NULL: the library
+                            allocates (cudaMalloc) and frees it itself. */
+  size_t workspace_bytes;
+} lbm_params;
+
+typedef struct lbm lbm; /* opaque handle; owns all device state it allocated */
+
+/* Bytes of device workspace a handle of this size and storage needs. */
+LBM_EXPORT lbm_status lbm_workspace_size(int nx, int ny, int nz, const lbm_params* p, size_t* bytes);
+
+/* Create a handle for an nx x ny x nz box (each >= 3) on the current CUDA
+ * device.  Validates and copies *p, derives alpha_r, sets the populations to
+ * the rest state of pure blue fluid (rho_b = rho_b0) and the time to 0.  The
+ * handle must be released with lbm_free(). */
+LBM_EXPORT lbm_status lbm_create(int nx, int ny, int nz, const lbm_params* p, lbm** out);
+
+/* Initial state (t = 0): f^k = f^{k(e)}(rho_k, u, alpha_k) of Eq. (EES) with
+ * Phi = 0.  rhoR, rhoB: N doubles each; u: 3N doubles or NULL for rest.
+ * Host or device pointers.  Resets the outflow plane history. */
+LBM_EXPORT lbm_status lbm_init_fields(lbm* h, const double* rhoR, const double* rhoB, const double* u);
+
+/* Circular equilibrium inlet of Sec. IV.A on the z = 0 plane: the nodes with
+ * (x-xc)^2 + (y-yc)^2 < (D/2)^2 emit f^r = f^{r(e)}(rho_r0, u_in, alpha_r)
+ * (Phi = 0) and f^b = 0 every step, u_in = (0, 0, u_j0) plus, per node, step
+ * and component, u_j0 * noise_frac * xi with xi uniform in [-1, 1) from
+ * SplitMix64 keyed by (seed, step, node index, component).  Requires
+ * bc[4] == LBM_BC_INFLOW_WALL.  D <= 0 removes the inlet. */
+LBM_EXPORT lbm_status lbm_set_inflow(lbm* h, double xc, double yc, double D, double u_j0, double noise_frac);
+
+/* Enqueue n >= 0 time steps: per step a density/phase-field pass, the fused
+ * collide-perturb-recolour-stream pass (in place, AA pattern) and, with an
+ * outflow face, the convective outflow update.  Asynchronous: returns after
+ * enqueueing.  Returns LBM_EUNSTABLE if a watchdog flag raised by earlier
+ * steps has already been observed by a synchronising call. */
+LBM_EXPORT lbm_status lbm_step(lbm* h, int n);
+
+/* Macroscopic fields at the current time: rho_r, rho_b (N each) and
+ * u = (sum_i sum_k f_i^k c_i + F/2)/rho (3N), Eq. (Momentum).  Any output
+ * pointer may be NULL.  Host or device pointers.  Synchronises. */
+LBM_EXPORT lbm_status lbm_macro(lbm* h, double* rhoR, double* rhoB, double* u);
+
+/* Diagnostics at the current time, reduced on the device in FP64 with a
+ * fixed summation order (bitwise reproducible):
+ *   mass_rb[2]       sum of rho_r and of rho_b over all nodes;
+ *   z_leading_edge   largest z of a node with phi > 0, refined by linear
+ *                    interpolation of the phi = 0 crossing towards z+1
+ *                    (-1 if no node has phi > 0);
+ *   dp_laplace       mean pressure over nodes with phi > 0.99 minus mean over
+ *                    nodes with phi < -0.99, p = sum_k rho_k 9(1-alpha_k)/19
+ *                    (Eq. press); 0 if either set is empty.
+ * Host pointers; any may be NULL.  Synchronises. */
+LBM_EXPORT lbm_status lbm_diag(lbm* h, double* mass_rb, double* z_leading_edge, double* dp_laplace);
+
+/* Copy out / in the post-streaming populations ([2][27][nz][ny][nx], see the
+ * conventions above).  lbm_set_populations also sets the time to t >= 0 and
+ * the outflow plane history to the given top plane.  Host or device
+ * pointers.  In F16/BF16 storage the values are decoded / encoded. */
+LBM_EXPORT lbm_status lbm_get_populations(lbm* h, double* f);
+LBM_EXPORT lbm_status lbm_set_populations(lbm* h, const double* f, long long t);
+
+/* Take n >= 1 steps with direct kernel launches, timing each launch with CUDA
+ * events recorded on the handle's stream (the stream the kernels run on).
+ * ms_out[0..2] receive the mean device time per launch, in milliseconds, of
+ * the density pass, the collide-stream pass and the outflow pass (0 when the
+ * box has no outflow face).  Synchronises; advances the time by n. */
+LBM_EXPORT lbm_status lbm_profile_step(lbm* h, int n, double* ms_out);
+
+/* Switch the stream later calls enqueue on (NULL = legacy default stream). */
+LBM_EXPORT lbm_status lbm_set_stream(lbm* h, void* cuda_stream);
+
+/* Wait for the handle's stream; reports LBM_EUNSTABLE if the watchdog fired. */
+LBM_EXPORT lbm_status lbm_synchronize(lbm* h);
+
+/* Current time step index t (number of steps taken since initialisation). */
+LBM_EXPORT long long lbm_time(const lbm* h);
+
+/* Number of kernel launches one lbm_step(h, 1) enqueues. */
+LBM_EXPORT int lbm_kernels_per_step(const lbm* h);
+
+/* Last error message of this handle ("" if none); valid until the next call. */
+LBM_EXPORT const char* lbm_last_error(const lbm* h);
+
+/* Name of a status code. */
+LBM_EXPORT const char* lbm_status_string(lbm_status s);
+
+/* The 27x27 transformation matrix M the kernels apply (row-major; row j is
+ * moment j+1 of Eq. momentSet, column i is the paper's direction i+1), for
+ * checking against App. A.  Host-only: needs no GPU. */
+LBM_EXPORT lbm_status lbm_moment_matrix(double* M);
+
+/* Check the library's own lattice tables on the host (moment basis against
+ * Eq. momentSet, orthogonality, weights, velocity order).  Needs no GPU.
+ * Returns LBM_OK or LBM_EINVAL with a message in *msg (static storage). */
+LBM_EXPORT lbm_status lbm_selfcheck(const char** msg);
+
+/* Release the handle and all device memory it allocated (not a caller
+ * workspace).  NULL is a no-op. */
+LBM_EXPORT void lbm_free(lbm* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

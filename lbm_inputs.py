@@ -163,11 +163,14 @@ def initial_fields(work, seed=None, u_amp=0.0):
 def parity_cases():
     """Small boxes (several tiles, ragged tails) that exercise every boundary type."""
     cases = []
+    # tau = 1 static droplet: unit rates for the non-conserved moments (Suga's set amplifies a
+    # mode at rest for tau = 1; the paper's own cases all have tau < 0.56)
     c1 = static_droplet()
-    cases.append(("static_droplet_32", c1, 0.0))
+    c1["params"]["s"] = uniform_rates(1.0)
+    cases.append(("static_droplet_32", c1, 0.01))
     # ragged box, unequal densities and viscosities, mixed faces, smooth random velocity
     w = dict(name="ragged_mixed", shape=(37, 11, 13),
-             params=_base(rho_r0=1.5, rho_b0=1.0, nu_r=0.05, nu_b=0.02, A=0.01, beta=0.7,
+             params=_base(rho_r0=1.5, rho_b0=1.0, nu_r=0.015, nu_b=0.008, A=0.01, beta=0.7,
                           bc=(PERIODIC, PERIODIC, FREESLIP, FREESLIP, NOSLIP, NOSLIP)),
              fields=("random_blobs", dict(seed=7, blobs=3)), steps=100)
     cases.append(("ragged_mixed", w, 0.02))

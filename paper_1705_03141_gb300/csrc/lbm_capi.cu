@@ -1,0 +1,639 @@
+// Host implementation of the C ABI declared in include/lbm.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "../../include/lbm.h"
+#include "lbm_dispatch.h"
+#include "lbm_kernels.cuh"
+
+using lbmk::Geom;
+using lbmk::KernelSet;
+using lbmk::Phys;
+
+namespace {
+
+constexpr int kGraphSteps = 16;  // steps per captured CUDA graph
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {  // byte offsets inside the device workspace
+  size_t pop, dens, top, counter, flag, partial, diag_out, scratch, total;
+};
+
+}  // namespace
+
+struct lbm {
+  int nx, ny, nz;
+  int64_t N;
+  lbm_params p;
+  const KernelSet* ks;
+  Geom G;
+  Phys P;
+  Layout L;
+  char* ws;
+  bool own_ws;
+  void *pop, *dens, *top, *partial;
+  long long* counter;
+  int* flag;
+  double *diag_out, *scratch;
+  int diag_blocks;
+  cudaStream_t stream;
+  cudaStream_t cap_stream;
+  cudaGraphExec_t graph[2];  // kGraphSteps steps starting at an even / odd step
+  long long t;
+  bool unstable;
+  std::string err;
+};
+
+namespace {
+
+lbm_status fail(lbm* h, lbm_status s, const char* fmt, ...) {
+  if (h) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    h->err = buf;
+  }
+  return s;
+}
+
+#define LBM_CUDA(h, call)                                                                          \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail((h), LBM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+const KernelSet* kernels_for(int storage) {
+  switch (storage) {
+    case LBM_STORE_F64: return lbmk::kernels_f64();
+    case LBM_STORE_F32: return lbmk::kernels_f32();
+    case LBM_STORE_F16: return lbmk::kernels_f16();
+    case LBM_STORE_BF16: return lbmk::kernels_bf16();
+    default: return nullptr;
+  }
+}
+
+// |M_j|^2 of the moment rows as the kernels apply them (M^-1 = M^T diag(1/|M_j|^2)).
+void row_norms(double d[27]) {
+  static double M[27][27];
+  lbmk::moment_matrix_tensor(M);
+  for (int j = 0; j < 27; ++j) {
+    double s = 0.0;
+    for (int t = 0; t < 27; ++t) s += M[j][t] * M[j][t];
+    d[j] = s;
+  }
+}
+
+const char* validate(int nx, int ny, int nz, const lbm_params* p) {
+  if (!p) return "params is NULL";
+  if (nx < 3 || ny < 3 || nz < 3) return "each box dimension must be >= 3";
+  if ((double)nx * ny * nz >= 2147483647.0 / 2) return "box too large (nx*ny*nz must stay below 2^30)";
+  if (!(p->rho_r0 > 0) || !(p->rho_b0 > 0)) return "rho_r0 and rho_b0 must be > 0";
+  const double ab = 8.0 / 27.0, ar = 1.0 - (1.0 - ab) / (p->rho_r0 / p->rho_b0);
+  if (!(ar >= 0.0 && ar < 1.0)) return "density ratio rho_r0/rho_b0 must be >= 19/27 (alpha_r in [0,1))";
+  if (!(p->nu_r > 0) || !(p->nu_b > 0)) return "nu_r and nu_b must be > 0";
+  if (!(p->A >= 0) || !(p->beta >= 0 && p->beta <= 1)) return "need A >= 0 and 0 <= beta <= 1";
+  for (int j = 4; j < 27; ++j) {
+    if (j >= 5 && j <= 9) continue;  // shear slots come from the viscosity
+    if (!(p->s[j] >= 0.0 && p->s[j] < 2.0)) return "relaxation rates must lie in [0, 2)";
+    for (int k = 4; k < j; ++k)
+      if (lbmk::kslot_of(k) == lbmk::kslot_of(j) && p->s[k] != p->s[j])
+        return "moments of one relaxation slot of K must share one rate";
+  }
+  if (p->force_mode < 0 || p->force_mode > 3) return "unknown force_mode";
+  for (int f = 0; f < 6; ++f)
+    if (p->bc[f] < 0 || p->bc[f] > 4) return "unknown boundary code";
+  for (int a = 0; a < 3; ++a)
+    if ((p->bc[2 * a] == LBM_BC_PERIODIC) != (p->bc[2 * a + 1] == LBM_BC_PERIODIC))
+      return "periodic faces must come in pairs";
+  for (int f = 0; f < 6; ++f) {
+    if (p->bc[f] == LBM_BC_INFLOW_WALL && f != 4) return "INFLOW_WALL is only allowed on the -z face";
+    if (p->bc[f] == LBM_BC_OUTFLOW && f != 5) return "OUTFLOW is only allowed on the +z face";
+  }
+  if (p->storage < 0 || p->storage > 3) return "unknown storage";
+  return nullptr;
+}
+
+Layout plan(int nx, int ny, int nz, const lbm_params* p, const KernelSet* ks, int64_t* Ns_out, int* diag_blocks) {
+  const int64_t N = (int64_t)nx * ny * nz;
+  const int64_t Ns = (int64_t)align_up((size_t)nx * ny * (nz + 2), 64);
+  const int64_t Pn = (int64_t)nx * ny;
+  int nb = (int)((N + lbmk::DIAG_THREADS - 1) / lbmk::DIAG_THREADS);
+  if (nb > 152 * 8) nb = 152 * 8;
+  Layout L;
+  size_t o = 0;
+  L.pop = o;
+  o = align_up(o + (size_t)ks->pop_planes * 27 * Ns * ks->pop_elem_bytes, 256);
+  L.dens = o;
+  o = align_up(o + (size_t)N * ks->dens_bytes, 256);
+  L.top = o;
+  if (p->bc[5] == LBM_BC_OUTFLOW) o = align_up(o + (size_t)2 * 27 * Pn * ks->real_bytes, 256);
+  L.counter = o;
+  o = align_up(o + sizeof(long long), 256);
+  L.flag = o;
+  o = align_up(o + sizeof(int), 256);
+  L.partial = o;
+  o = align_up(o + (size_t)nb * lbmk::DIAG_VALS * sizeof(double), 256);
+  L.diag_out = o;
+  o = align_up(o + lbmk::DIAG_VALS * sizeof(double), 256);
+  L.scratch = o;
+  o = align_up(o + (size_t)5 * N * sizeof(double), 256);
+  L.total = o;
+  if (Ns_out) *Ns_out = Ns;
+  if (diag_blocks) *diag_blocks = nb;
+  return L;
+}
+
+__global__ void k_fill(double* a, int64_t n, double v) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+
+bool is_device_ptr(const void* ptr) {
+  if (!ptr) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void drop_graphs(lbm* h) {
+  for (int k = 0; k < 2; ++k)
+    if (h->graph[k]) {
+      cudaGraphExecDestroy(h->graph[k]);
+      h->graph[k] = nullptr;
+    }
+}
+
+// enqueue one time step (the step with index h->t) on stream s
+lbm_status enqueue_step(lbm* h, long long t, cudaStream_t s) {
+  const int layout = (int)(t & 1);
+  LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, h->counter, s));
+  LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, s));
+  if (h->p.bc[5] == LBM_BC_OUTFLOW) LBM_CUDA(h, h->ks->outflow(h->pop, h->G, h->P, (int)((t + 1) & 1), h->top, s));
+  return LBM_OK;
+}
+
+lbm_status build_graph(lbm* h, int parity) {
+  cudaGraph_t g = nullptr;
+  LBM_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  lbm_status st = LBM_OK;
+  for (int k = 0; k < kGraphSteps && st == LBM_OK; ++k) st = enqueue_step(h, parity + k, h->cap_stream);
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+  if (st != LBM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(h, LBM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&h->graph[parity], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->graph[parity] = nullptr;
+    return fail(h, LBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  return LBM_OK;
+}
+
+lbm_status check_flag(lbm* h) {
+  int flag = 0;
+  LBM_CUDA(h, cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (flag) h->unstable = true;
+  if (h->unstable) return fail(h, LBM_EUNSTABLE, "watchdog: non-finite or non-positive density seen");
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_status_string(lbm_status s) {
+  switch (s) {
+    case LBM_OK: return "LBM_OK";
+    case LBM_EINVAL: return "LBM_EINVAL";
+    case LBM_ENOMEM: return "LBM_ENOMEM";
+    case LBM_ECUDA: return "LBM_ECUDA";
+    case LBM_EUNSTABLE: return "LBM_EUNSTABLE";
+    case LBM_ETIMEOUT: return "LBM_ETIMEOUT";
+    case LBM_ESTATE: return "LBM_ESTATE";
+  }
+  return "unknown";
+}
+
+lbm_status lbm_workspace_size(int nx, int ny, int nz, const lbm_params* p, size_t* bytes) {
+  if (!bytes || validate(nx, ny, nz, p)) return LBM_EINVAL;
+  *bytes = plan(nx, ny, nz, p, kernels_for(p->storage), nullptr, nullptr).total;
+  return LBM_OK;
+}
+
+lbm_status lbm_create(int nx, int ny, int nz, const lbm_params* p, lbm** out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  if (validate(nx, ny, nz, p)) return LBM_EINVAL;
+  lbm* h = new (std::nothrow) lbm();
+  if (!h) return LBM_ENOMEM;
+  h->nx = nx;
+  h->ny = ny;
+  h->nz = nz;
+  h->N = (int64_t)nx * ny * nz;
+  h->p = *p;
+  h->ks = kernels_for(p->storage);
+  int64_t Ns = 0;
+  h->L = plan(nx, ny, nz, p, h->ks, &Ns, &h->diag_blocks);
+  h->stream = static_cast<cudaStream_t>(p->cuda_stream);
+
+  Geom& G = h->G;
+  G.nx = nx;
+  G.ny = ny;
+  G.nz = nz;
+  G.Ns = Ns;
+  for (int f = 0; f < 6; ++f) G.bc[f] = p->bc[f];
+  G.inflow = 0;
+  G.xc = G.yc = G.r2 = 0.0;
+
+  Phys& P = h->P;
+  memset(&P, 0, sizeof P);
+  P.rho_r0 = p->rho_r0;
+  P.rho_b0 = p->rho_b0;
+  P.alpha_b = 8.0 / 27.0;  // Sec. II: alpha_b = 8/27, c_s^b = 1/sqrt(3)
+  P.alpha_r = 1.0 - (1.0 - P.alpha_b) / (p->rho_r0 / p->rho_b0);  // gamma = (1-alpha_b)/(1-alpha_r)
+  P.nu_r = p->nu_r;
+  P.nu_b = p->nu_b;
+  P.A = p->A;
+  P.beta = p->beta;
+  double d[27];
+  row_norms(d);
+  for (int j = 0; j < 27; ++j) {
+    P.invd[j] = 1.0 / d[j];
+    P.kd[j] = (j < 4) ? 0.0 : p->s[j] / d[j];
+  }
+  for (int a = 0; a < 3; ++a) P.g[a] = p->g[a];
+  P.force_mode = p->force_mode;
+  P.rho_ref = p->force_mode == LBM_FORCE_BUOYANCY ? 0.5 * (p->rho_r0 + p->rho_b0) : p->rho_b0;
+  P.seed = p->seed;
+  for (int t = 0; t < 27; ++t) {
+    const double w = lbmk::weight_of(t);
+    P.refR[t] = p->rho_r0 * (t == lbmk::REST ? P.alpha_r : 27.0 / 19.0 * (1.0 - P.alpha_r) * w);
+    P.refB[t] = p->rho_b0 * (t == lbmk::REST ? P.alpha_b : 27.0 / 19.0 * (1.0 - P.alpha_b) * w);
+  }
+
+  if (p->workspace) {
+    if (p->workspace_bytes < h->L.total) {
+      delete h;
+      return LBM_ENOMEM;
+    }
+    if (((uintptr_t)p->workspace) % 256) {
+      delete h;
+      return LBM_EINVAL;
+    }
+    h->ws = static_cast<char*>(p->workspace);
+    h->own_ws = false;
+  } else {
+    void* mem = nullptr;
+    if (cudaMalloc(&mem, h->L.total) != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return LBM_ENOMEM;
+    }
+    h->ws = static_cast<char*>(mem);
+    h->own_ws = true;
+  }
+  h->pop = h->ws + h->L.pop;
+  h->dens = h->ws + h->L.dens;
+  h->top = h->ws + h->L.top;
+  h->counter = reinterpret_cast<long long*>(h->ws + h->L.counter);
+  h->flag = reinterpret_cast<int*>(h->ws + h->L.flag);
+  h->partial = h->ws + h->L.partial;
+  h->diag_out = reinterpret_cast<double*>(h->ws + h->L.diag_out);
+  h->scratch = reinterpret_cast<double*>(h->ws + h->L.scratch);
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    if (h->own_ws) cudaFree(h->ws);
+    delete h;
+    return LBM_ECUDA;
+  }
+  // initial state: pure blue fluid at rest
+  {
+    double* rr = h->scratch;
+    double* rb = h->scratch + h->N;
+    const unsigned nb = (unsigned)((h->N + 255) / 256);
+    k_fill<<<nb, 256, 0, h->stream>>>(rr, h->N, 0.0);
+    k_fill<<<nb, 256, 0, h->stream>>>(rb, h->N, p->rho_b0);
+    lbm_status st = cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+    if (st == LBM_OK) st = lbm_init_fields(h, rr, rb, nullptr);
+    if (st != LBM_OK) {
+      cudaGetLastError();
+      lbm_free(h);
+      return st;
+    }
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+lbm_status lbm_init_fields(lbm* h, const double* rhoR, const double* rhoB, const double* u) {
+  if (!h) return LBM_EINVAL;
+  if (!rhoR || !rhoB) return fail(h, LBM_EINVAL, "rhoR and rhoB are required");
+  const int64_t N = h->N;
+  const double *dr = rhoR, *db = rhoB, *du = u;
+  double* sr = h->scratch;
+  double* sb = h->scratch + N;
+  double* su = h->scratch + 2 * N;
+  // stage host inputs (device inputs may alias the scratch: copy them in order)
+  if (!is_device_ptr(rhoR)) {
+    LBM_CUDA(h, cudaMemcpyAsync(sr, rhoR, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+    dr = sr;
+  }
+  if (!is_device_ptr(rhoB)) {
+    LBM_CUDA(h, cudaMemcpyAsync(sb, rhoB, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+    db = sb;
+  }
+  if (u && !is_device_ptr(u)) {
+    LBM_CUDA(h, cudaMemcpyAsync(su, u, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, h->stream));
+    du = su;
+  }
+  LBM_CUDA(h, h->ks->init(h->pop, h->G, h->P, dr, db, du, h->stream));
+  h->t = 0;
+  const long long c0 = -1;
+  LBM_CUDA(h, cudaMemcpyAsync(h->counter, &c0, sizeof c0, cudaMemcpyHostToDevice, h->stream));
+  LBM_CUDA(h, cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+  if (h->p.bc[5] == LBM_BC_OUTFLOW) LBM_CUDA(h, h->ks->top_from_state(h->pop, h->G, h->P, 0, h->top, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->unstable = false;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_inflow(lbm* h, double xc, double yc, double D, double u_j0, double noise_frac) {
+  if (!h) return LBM_EINVAL;
+  if (h->p.bc[4] != LBM_BC_INFLOW_WALL) return fail(h, LBM_ESTATE, "the -z face is not LBM_BC_INFLOW_WALL");
+  if (!(isfinite(xc) && isfinite(yc) && isfinite(D) && isfinite(u_j0) && isfinite(noise_frac)) || noise_frac < 0)
+    return fail(h, LBM_EINVAL, "inlet parameters must be finite, noise_frac >= 0");
+  if (!(fabs(u_j0) < 0.5)) return fail(h, LBM_EINVAL, "|u_j0| must stay below 0.5 lattice units");
+  h->G.inflow = D > 0 ? 1 : 0;
+  h->G.xc = xc;
+  h->G.yc = yc;
+  h->G.r2 = D > 0 ? 0.25 * D * D : 0.0;
+  h->P.u_j0 = u_j0;
+  h->P.noise_frac = noise_frac;
+  drop_graphs(h);
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm* h, int n) {
+  if (!h || n < 0) return h ? fail(h, LBM_EINVAL, "n must be >= 0") : LBM_EINVAL;
+  if (h->unstable) return fail(h, LBM_EUNSTABLE, "watchdog: non-finite or non-positive density seen");
+  static const bool no_graphs = getenv("LBM_NO_GRAPHS") != nullptr;
+  int k = 0;
+  if (!no_graphs && n >= kGraphSteps) {
+    const int parity = (int)(h->t & 1);
+    if (!h->graph[parity]) {
+      lbm_status st = build_graph(h, parity);
+      if (st != LBM_OK) return st;
+    }
+    for (; k + kGraphSteps <= n; k += kGraphSteps) {
+      LBM_CUDA(h, cudaGraphLaunch(h->graph[parity], h->stream));
+      h->t += kGraphSteps;
+    }
+  }
+  for (; k < n; ++k) {
+    lbm_status st = enqueue_step(h, h->t, h->stream);
+    if (st != LBM_OK) return st;
+    h->t += 1;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_macro(lbm* h, double* rhoR, double* rhoB, double* u) {
+  if (!h) return LBM_EINVAL;
+  const int64_t N = h->N;
+  const int layout = (int)(h->t & 1);
+  double* dr = rhoR ? (is_device_ptr(rhoR) ? rhoR : h->scratch) : nullptr;
+  double* db = rhoB ? (is_device_ptr(rhoB) ? rhoB : h->scratch + N) : nullptr;
+  double* du = u ? (is_device_ptr(u) ? u : h->scratch + 2 * N) : nullptr;
+  LBM_CUDA(h, h->ks->macro(h->pop, h->G, h->P, layout, dr, db, du, h->stream));
+  if (rhoR && dr != rhoR) LBM_CUDA(h, cudaMemcpyAsync(rhoR, dr, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+  if (rhoB && db != rhoB) LBM_CUDA(h, cudaMemcpyAsync(rhoB, db, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+  if (u && du != u) LBM_CUDA(h, cudaMemcpyAsync(u, du, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, h->stream));
+  return check_flag(h);
+}
+
+lbm_status lbm_diag(lbm* h, double* mass_rb, double* z_leading_edge, double* dp_laplace) {
+  if (!h) return LBM_EINVAL;
+  const int64_t N = h->N;
+  const int layout = (int)(h->t & 1);
+  double* rr = h->scratch;
+  double* rb = h->scratch + N;
+  LBM_CUDA(h, h->ks->macro(h->pop, h->G, h->P, layout, rr, rb, nullptr, h->stream));
+  lbmk::k_diag_partial<<<h->diag_blocks, lbmk::DIAG_THREADS, 0, h->stream>>>(
+      h->G, h->P.alpha_r, h->P.alpha_b, rr, rb, static_cast<double*>(h->partial));
+  LBM_CUDA(h, cudaGetLastError());
+  lbmk::k_diag_final<<<1, 32 * lbmk::DIAG_VALS, 0, h->stream>>>(h->diag_blocks, static_cast<double*>(h->partial),
+                                                                 h->diag_out);
+  LBM_CUDA(h, cudaGetLastError());
+  double v[lbmk::DIAG_VALS];
+  LBM_CUDA(h, cudaMemcpyAsync(v, h->diag_out, sizeof v, cudaMemcpyDeviceToHost, h->stream));
+  lbm_status st = check_flag(h);
+  if (st != LBM_OK) return st;
+  if (mass_rb) {
+    mass_rb[0] = v[0];
+    mass_rb[1] = v[1];
+  }
+  if (z_leading_edge) *z_leading_edge = v[6];
+  if (dp_laplace) *dp_laplace = (v[3] > 0 && v[5] > 0) ? v[2] / v[3] - v[4] / v[5] : 0.0;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm* h, double* f) {
+  if (!h) return LBM_EINVAL;
+  if (!f) return fail(h, LBM_EINVAL, "f is NULL");
+  const int64_t N = h->N;
+  const int layout = (int)(h->t & 1);
+  const bool dev = is_device_ptr(f);
+  for (int i = 0; i < 27; ++i) {
+    double* outr = dev ? f + (int64_t)i * N : h->scratch;
+    double* outb = dev ? f + (int64_t)(27 + i) * N : h->scratch + N;
+    LBM_CUDA(h, h->ks->get_pop(h->pop, h->G, h->P, layout, i, outr, outb, h->stream));
+    if (!dev) {
+      LBM_CUDA(h, cudaMemcpyAsync(f + (int64_t)i * N, outr, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+      LBM_CUDA(h, cudaMemcpyAsync(f + (int64_t)(27 + i) * N, outb, sizeof(double) * N, cudaMemcpyDeviceToHost,
+                                  h->stream));
+    }
+  }
+  return check_flag(h);
+}
+
+lbm_status lbm_set_populations(lbm* h, const double* f, long long t) {
+  if (!h) return LBM_EINVAL;
+  if (!f || t < 0) return fail(h, LBM_EINVAL, "f is NULL or t < 0");
+  const int64_t N = h->N;
+  const int layout = (int)(t & 1);
+  const bool dev = is_device_ptr(f);
+  for (int i = 0; i < 27; ++i) {
+    const double* inr = f + (int64_t)i * N;
+    const double* inb = f + (int64_t)(27 + i) * N;
+    if (!dev) {
+      LBM_CUDA(h, cudaMemcpyAsync(h->scratch, inr, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+      LBM_CUDA(h, cudaMemcpyAsync(h->scratch + N, inb, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+      inr = h->scratch;
+      inb = h->scratch + N;
+    }
+    LBM_CUDA(h, h->ks->set_pop(h->pop, h->G, h->P, layout, i, inr, inb, h->stream));
+  }
+  h->t = t;
+  const long long c0 = t - 1;
+  LBM_CUDA(h, cudaMemcpyAsync(h->counter, &c0, sizeof c0, cudaMemcpyHostToDevice, h->stream));
+  LBM_CUDA(h, cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+  if (h->p.bc[5] == LBM_BC_OUTFLOW) LBM_CUDA(h, h->ks->top_from_state(h->pop, h->G, h->P, layout, h->top, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->unstable = false;
+  return LBM_OK;
+}
+
+lbm_status lbm_profile_step(lbm* h, int n, double* ms_out) {
+  if (!h) return LBM_EINVAL;
+  if (n < 1 || !ms_out) return fail(h, LBM_EINVAL, "need n >= 1 and an output array of 3 doubles");
+  if (h->unstable) return fail(h, LBM_EUNSTABLE, "watchdog: non-finite or non-positive density seen");
+  const bool outflow = h->p.bc[5] == LBM_BC_OUTFLOW;
+  const int per = 4;
+  cudaEvent_t* ev = (cudaEvent_t*)calloc((size_t)per * n, sizeof(cudaEvent_t));
+  if (!ev) return fail(h, LBM_ENOMEM, "event array");
+  lbm_status st = LBM_OK;
+  int made = 0;
+  for (; made < per * n; ++made)
+    if (cudaEventCreate(&ev[made]) != cudaSuccess) {
+      st = fail(h, LBM_ECUDA, "cudaEventCreate failed");
+      break;
+    }
+  for (int k = 0; st == LBM_OK && k < n; ++k) {
+    const long long t = h->t;
+    const int layout = (int)(t & 1);
+    cudaEvent_t* e = ev + per * k;
+    if (cudaEventRecord(e[0], h->stream) != cudaSuccess ||
+        h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, h->counter, h->stream) != cudaSuccess ||
+        cudaEventRecord(e[1], h->stream) != cudaSuccess ||
+        h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->stream) != cudaSuccess ||
+        cudaEventRecord(e[2], h->stream) != cudaSuccess ||
+        (outflow && h->ks->outflow(h->pop, h->G, h->P, (int)((t + 1) & 1), h->top, h->stream) != cudaSuccess) ||
+        cudaEventRecord(e[3], h->stream) != cudaSuccess) {
+      st = fail(h, LBM_ECUDA, "profiled step launch: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    h->t += 1;
+  }
+  if (st == LBM_OK && cudaStreamSynchronize(h->stream) != cudaSuccess)
+    st = fail(h, LBM_ECUDA, "synchronize: %s", cudaGetErrorString(cudaGetLastError()));
+  if (st == LBM_OK) {
+    double acc[3] = {0, 0, 0};
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < 3; ++j) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[per * k + j], ev[per * k + j + 1]);
+        acc[j] += ms;
+      }
+    for (int j = 0; j < 3; ++j) ms_out[j] = acc[j] / n;
+    if (!outflow) ms_out[2] = 0.0;
+  }
+  for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+  free(ev);
+  if (st != LBM_OK) return st;
+  return check_flag(h);
+}
+
+lbm_status lbm_set_stream(lbm* h, void* cuda_stream) {
+  if (!h) return LBM_EINVAL;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->p.cuda_stream = cuda_stream;
+  return LBM_OK;
+}
+
+lbm_status lbm_synchronize(lbm* h) {
+  if (!h) return LBM_EINVAL;
+  return check_flag(h);
+}
+
+long long lbm_time(const lbm* h) { return h ? h->t : -1; }
+
+int lbm_kernels_per_step(const lbm* h) {
+  if (!h) return -1;
+  return 2 + (h->p.bc[5] == LBM_BC_OUTFLOW ? 1 : 0);
+}
+
+const char* lbm_last_error(const lbm* h) { return h ? h->err.c_str() : "NULL handle"; }
+
+lbm_status lbm_moment_matrix(double* M) {
+  if (!M) return LBM_EINVAL;
+  static double Mt[27][27];
+  lbmk::moment_matrix_tensor(Mt);
+  for (int j = 0; j < 27; ++j)
+    for (int i = 0; i < 27; ++i) M[27 * j + i] = Mt[j][lbmk::paper_to_tensor(i)];
+  return LBM_OK;
+}
+
+lbm_status lbm_selfcheck(const char** msg) {
+  static char buf[256];
+  const char* ok = "ok";
+  if (msg) *msg = ok;
+  static double M[27][27];
+  lbmk::moment_matrix_tensor(M);
+  // every paper direction maps to a distinct tensor index
+  int seen[27] = {0};
+  for (int i = 0; i < 27; ++i) seen[lbmk::paper_to_tensor(i)]++;
+  for (int t = 0; t < 27; ++t)
+    if (seen[t] != 1) {
+      if (msg) *msg = "paper_to_tensor is not a permutation";
+      return LBM_EINVAL;
+    }
+  // rows 1-4 are the conserved moments <1>, <c_x>, <c_y>, <c_z>
+  for (int t = 0; t < 27; ++t) {
+    const double want[4] = {1.0, (double)lbmk::cx_of(t), (double)lbmk::cy_of(t), (double)lbmk::cz_of(t)};
+    for (int j = 0; j < 4; ++j)
+      if (M[j][t] != want[j]) {
+        snprintf(buf, sizeof buf, "row %d of M is not the conserved moment", j + 1);
+        if (msg) *msg = buf;
+        return LBM_EINVAL;
+      }
+  }
+  // rows mutually orthogonal (the inverse used by the kernels relies on it)
+  for (int a = 0; a < 27; ++a)
+    for (int b = 0; b < a; ++b) {
+      double s = 0.0;
+      for (int t = 0; t < 27; ++t) s += M[a][t] * M[b][t];
+      if (s != 0.0) {
+        snprintf(buf, sizeof buf, "rows %d and %d of M are not orthogonal", a + 1, b + 1);
+        if (msg) *msg = buf;
+        return LBM_EINVAL;
+      }
+    }
+  // weights: sum 1, second moment 1/3
+  double sw = 0.0, s2 = 0.0;
+  for (int t = 0; t < 27; ++t) {
+    sw += lbmk::weight_of(t);
+    s2 += lbmk::weight_of(t) * lbmk::cx_of(t) * lbmk::cx_of(t);
+  }
+  if (fabs(sw - 1.0) > 1e-15 || fabs(s2 - 1.0 / 3.0) > 1e-15) {
+    if (msg) *msg = "weights do not satisfy sum w = 1, sum w c_x^2 = 1/3";
+    return LBM_EINVAL;
+  }
+  return LBM_OK;
+}
+
+void lbm_free(lbm* h) {
+  if (!h) return;
+  drop_graphs(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->own_ws && h->ws) cudaFree(h->ws);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,36 @@
+// Host-side table of kernel launchers for one storage type (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmk {
+struct Geom;
+struct Phys;
+
+struct KernelSet {
+  size_t pop_elem_bytes;  // bytes per stored value
+  int pop_planes;         // stored planes per direction (2 plain, 1 packed)
+  size_t dens_bytes;      // bytes per node of the pass-1 field
+  size_t real_bytes;      // bytes of the compute type (outflow plane history)
+  cudaError_t (*density)(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag,
+                         long long* step_counter, cudaStream_t s);
+  cudaError_t (*collide)(void* pop, const Geom& G, const Phys& P, int odd, const void* dens,
+                         const long long* step_counter, cudaStream_t s);
+  cudaError_t (*outflow)(void* pop, const Geom& G, const Phys& P, int layout, void* top, cudaStream_t s);
+  cudaError_t (*init)(void* pop, const Geom& G, const Phys& P, const double* rr, const double* rb, const double* u,
+                      cudaStream_t s);
+  cudaError_t (*get_pop)(void* pop, const Geom& G, const Phys& P, int layout, int pdir, double* out_r, double* out_b,
+                         cudaStream_t s);
+  cudaError_t (*set_pop)(void* pop, const Geom& G, const Phys& P, int layout, int pdir, const double* in_r,
+                         const double* in_b, cudaStream_t s);
+  cudaError_t (*top_from_state)(void* pop, const Geom& G, const Phys& P, int layout, void* top, cudaStream_t s);
+  cudaError_t (*macro)(void* pop, const Geom& G, const Phys& P, int layout, double* rr, double* rb, double* u,
+                       cudaStream_t s);
+  int (*collide_regs)();  // registers per thread of the pass-2 kernel (from the function attributes)
+};
+
+const KernelSet* kernels_f64();
+const KernelSet* kernels_f32();
+const KernelSet* kernels_f16();
+const KernelSet* kernels_bf16();
+}  // namespace lbmk

@@ -1,0 +1,175 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+FP64 storage must match to 1e-12 relative on rho_r, rho_b and u (and the
+populations) after 100 steps on boxes that span several thread blocks with
+ragged tails and exercise every face type.  FP32 and the packed 16-bit
+storages are held to tolerances derived from their precision (see each test).
+"""
+import numpy as np
+import pytest
+
+import lbm_inputs as L
+import oracle
+import paper_1705_03141_gb300 as pkg
+
+pytestmark = pytest.mark.gpu
+
+CASES = {name: (w, u) for name, w, u in L.parity_cases()}
+
+
+def _pair(work, u_amp, storage, seed=11):
+    rr, rb, u = L.initial_fields(work, seed=seed, u_amp=u_amp)
+    lat = pkg.Lattice(work["shape"], work["params"], storage=storage)
+    lat.init_fields(rr, rb, u)
+    orc = oracle.Oracle(work["shape"], work["params"])
+    orc.init_fields(rr, rb, u)
+    return lat, orc
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp64_matches_oracle_100_steps(cuda, name):
+    work, u_amp = CASES[name]
+    lat, orc = _pair(work, u_amp, "f64")
+    for chunk in (1, 15, 16, 68):  # direct launches and CUDA-graph replays, both parities
+        lat.step(chunk)
+        orc.step(chunk)
+    assert lat.time == orc.t == 100
+    gr, gb, gu = lat.macro()
+    orr, orb, ou = orc.macro()
+    assert _rel(gr, orr) < 1e-12
+    assert _rel(gb, orb) < 1e-12
+    assert _rel(gu, ou) < 1e-12
+    assert _rel(lat.get_populations(), orc.f) < 1e-12
+    lat.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp32_matches_oracle(cuda, name):
+    """FP32 arithmetic and storage.  Each stored population is rounded to 2^-24 relative every step;
+    the 27 roundings that enter a node's momentum, accumulated as a random walk over 100 steps,
+    give sqrt(100 * 27) * 2^-24 * max(rho) ~ 3e-6 max(rho) on u.  Densities: 2e-5 of max(rho)."""
+    work, u_amp = CASES[name]
+    lat, orc = _pair(work, u_amp, "f32")
+    lat.step(100)
+    orc.step(100)
+    gr, gb, gu = lat.macro()
+    orr, orb, ou = orc.macro()
+    scale = max(np.max(np.abs(orr)), np.max(np.abs(orb)))
+    assert np.max(np.abs(gr - orr)) < 2e-5 * scale
+    assert np.max(np.abs(gb - orb)) < 2e-5 * scale
+    assert np.max(np.abs(gu - ou)) < 1e-4 * np.max(np.abs(ou)) + 3e-6 * scale
+    lat.close()
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("name", ["static_droplet_32", "rayleigh_taylor_16", "jet_24x20x40"])
+def test_packed_storage_error_budget(cuda, name, storage):
+    """16-bit deviation + 16-bit red fraction storage, FP32 arithmetic.  The deviation carries
+    2^-11 (half) or 2^-8 (bfloat16) relative error per store and the red fraction 2^-17 absolute;
+    after 100 steps the densities stay within 2e-3 (half) / 1e-2 (bfloat16) of the oracle."""
+    work, u_amp = CASES[name]
+    lat, orc = _pair(work, u_amp, storage)
+    lat.step(100)
+    orc.step(100)
+    gr, gb, gu = lat.macro()
+    orr, orb, ou = orc.macro()
+    tol = 2e-3 if storage == "f16" else 1e-2
+    scale = max(np.max(np.abs(orr)), np.max(np.abs(orb)))
+    assert np.max(np.abs(gr - orr)) < tol * scale
+    assert np.max(np.abs(gb - orb)) < tol * scale
+    assert np.all(np.isfinite(gu))
+    lat.close()
+
+
+def test_graph_replay_equals_direct_launches(cuda):
+    work, u_amp = CASES["jet_24x20x40"]
+    rr, rb, u = L.initial_fields(work, seed=1, u_amp=u_amp)
+    a = pkg.Lattice(work["shape"], work["params"], storage="f32")
+    b = pkg.Lattice(work["shape"], work["params"], storage="f32")
+    a.init_fields(rr, rb, u)
+    b.init_fields(rr, rb, u)
+    a.step(37)  # two 16-step graphs + 5 direct steps
+    for _ in range(37):
+        b.step(1)
+    np.testing.assert_array_equal(a.get_populations(), b.get_populations())
+    a.close()
+    b.close()
+
+
+def test_set_populations_roundtrip_and_resume(cuda):
+    """lbm_set_populations at an odd time, then stepping, matches the oracle continuing from there."""
+    work, u_amp = CASES["ragged_mixed"]
+    lat, orc = _pair(work, u_amp, "f64")
+    orc.step(7)
+    lat.set_populations(orc.f, t=7)
+    np.testing.assert_array_equal(lat.get_populations(), orc.f)
+    lat.step(9)
+    orc.step(9)
+    assert _rel(lat.get_populations(), orc.f) < 1e-12
+    lat.close()
+
+
+def test_diag_matches_fields(cuda):
+    work, u_amp = CASES["static_droplet_32"]
+    lat, orc = _pair(work, u_amp, "f64")
+    lat.step(20)
+    orc.step(20)
+    d = lat.diag()
+    r, b, _ = orc.macro()
+    assert d["mass_r"] == pytest.approx(r.sum(), rel=1e-13)
+    assert d["mass_b"] == pytest.approx(b.sum(), rel=1e-13)
+    phi = (r - b) / (r + b)
+    ar = oracle.alpha_r(work["params"])
+    p = r * 9 * (1 - ar) / 19 + b * 9 * (1 - 8 / 27) / 19
+    assert d["dp"] == pytest.approx(p[phi > 0.99].mean() - p[phi < -0.99].mean(), rel=1e-9)
+    # leading edge: highest red node, refined towards the phi = 0 crossing
+    zs = []
+    nz = phi.shape[0]
+    for z, y, x in zip(*np.where(phi > 0)):
+        c = float(z)
+        if z < nz - 1 and phi[z + 1, y, x] <= 0:
+            c = z + phi[z, y, x] / (phi[z, y, x] - phi[z + 1, y, x])
+        zs.append(c)
+    assert d["z_le"] == pytest.approx(max(zs), rel=1e-12)
+    # bitwise reproducible
+    assert lat.diag() == d
+    lat.close()
+
+
+def test_degenerate_states(cuda):
+    """Pure blue fluid at rest stays exactly at rest; a single red phase has no interface terms."""
+    w = L.static_droplet(n=9, R=2.0)
+    lat = pkg.Lattice(w["shape"], w["params"], storage="f64")
+    f0 = lat.get_populations()
+    lat.step(5)
+    np.testing.assert_allclose(lat.get_populations(), f0, rtol=0, atol=1e-15)
+    lat.step(0)
+    assert lat.time == 5
+    lat.close()
+
+
+def test_device_buffers_and_torch_stream(cuda):
+    import torch
+
+    work, u_amp = CASES["rayleigh_taylor_16"]
+    rr, rb, u = L.initial_fields(work, seed=2, u_amp=u_amp)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        lat = pkg.Lattice(work["shape"], work["params"], storage="f64")
+        lat.init_fields(torch.from_numpy(rr).cuda(), torch.from_numpy(rb).cuda(), torch.from_numpy(u).cuda())
+        lat.step(10)
+        out = (torch.empty(rr.shape, dtype=torch.float64, device="cuda"),
+               torch.empty(rr.shape, dtype=torch.float64, device="cuda"),
+               torch.empty((3,) + rr.shape, dtype=torch.float64, device="cuda"))
+        lat.macro(out)
+    orc = oracle.Oracle(work["shape"], work["params"])
+    orc.init_fields(rr, rb, u)
+    orc.step(10)
+    orr, orb, ou = orc.macro()
+    assert _rel(out[0].cpu().numpy(), orr) < 1e-12
+    assert _rel(out[2].cpu().numpy(), ou) < 1e-12
+    lat.close()
