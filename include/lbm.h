@@ -217,6 +217,31 @@ LBM_EXPORT lbm_status lbm_moment_matrix(double* M);
  * Returns LBM_OK or LBM_EINVAL with a message in *msg (static storage). */
 LBM_EXPORT lbm_status lbm_selfcheck(const char** msg);
 
+/* Allocation-free diagnostics; the paper has no counterpart (it is an
+ * interface for callers, not part of the method).  Reduces caller-owned device
+ * fields rhoR, rhoB (N = nx*ny*nz doubles each, x fastest, e.g. filled by
+ * lbm_macro into device buffers) to out[0..3] = {mass_r, mass_b,
+ * z_leading_edge, dp_laplace}, defined exactly as in lbm_diag; rho_r0/rho_b0
+ * give alpha_r as in lbm_create.
+ * It exists for callers that cannot allocate device memory: code whose host
+ * framework owns every device allocation through its own pool, or loops that
+ * forbid cudaMalloc and the synchronisation it implies.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine.  Its only scratch, the
+ * per-block partial sums, is a static device array of 3.7 MB that every GPU
+ * loading this library holds until the process exits; boxes above 16,777,216
+ * nodes (65536 blocks of 256) are rejected with LBM_EINVAL.  The first call
+ * on a device looks up that array's device address (set-up): make that first
+ * call before any stream capture.  All calls share the array and leave their
+ * contents in it; every slot a call reads is written by the same call first,
+ * so nothing needs clearing, but calls that overlap on the GPU (several
+ * streams or host threads at once) race on it.  Work goes on cuda_stream
+ * (NULL = legacy default stream); out may be device memory, or host memory,
+ * in which case the call synchronises the stream.  *err (may be NULL) receives
+ * a static message. */
+LBM_EXPORT lbm_status lbm_diag_fields_static(const double* rhoR, const double* rhoB, int nx, int ny, int nz,
+                                             double rho_r0, double rho_b0, double* out, void* cuda_stream,
+                                             const char** err);
+
 /* Release the handle and all device memory it allocated (not a caller
  * workspace).  NULL is a no-op. */
 LBM_EXPORT void lbm_free(lbm* h);

@@ -26,7 +26,7 @@ Q = 27
 SYMBOLS = ["lbm_workspace_size", "lbm_create", "lbm_init_fields", "lbm_set_inflow", "lbm_step", "lbm_macro",
            "lbm_diag", "lbm_get_populations", "lbm_set_populations", "lbm_profile_step", "lbm_set_stream", "lbm_synchronize", "lbm_time",
            "lbm_kernels_per_step", "lbm_last_error", "lbm_status_string", "lbm_moment_matrix", "lbm_selfcheck",
-           "lbm_free"]
+           "lbm_diag_fields_static", "lbm_free"]
 
 
 class LbmError(RuntimeError):
@@ -85,6 +85,7 @@ def library():
         lib.lbm_status_string.restype = ctypes.c_char_p
         lib.lbm_moment_matrix.argtypes = [vp]
         lib.lbm_selfcheck.argtypes = [P(ctypes.c_char_p)]
+        lib.lbm_diag_fields_static.argtypes = [vp, vp, i, i, i, d, d, vp, vp, P(ctypes.c_char_p)]
         lib.lbm_free.argtypes = [h]
         lib.lbm_free.restype = None
         for name in SYMBOLS:
@@ -128,6 +129,25 @@ def selfcheck() -> str:
     if rc != 0:
         raise LbmError(rc, msg.value.decode())
     return msg.value.decode()
+
+
+def diag_fields_static(rho_r, rho_b, rho_r0, rho_b0, out=None, stream=None):
+    """Allocation-free FP64 diagnostics of device fields rho_r, rho_b (torch float64 CUDA tensors,
+    shape (nz, ny, nx)): (mass_r, mass_b, z_leading_edge, dp_laplace).  Its scratch is a static
+    device array inside the library; see lbm_diag_fields_static in include/lbm.h."""
+    import torch
+
+    nz, ny, nx = rho_r.shape
+    host = out is None
+    if host:
+        out = np.zeros(4)
+    st = torch.cuda.current_stream() if stream is None else stream
+    msg = ctypes.c_char_p()
+    rc = library().lbm_diag_fields_static(_ptr(rho_r), _ptr(rho_b), int(nx), int(ny), int(nz), float(rho_r0),
+                                          float(rho_b0), _ptr(out), st.cuda_stream, ctypes.byref(msg))
+    if rc != 0:
+        raise LbmError(rc, (msg.value or b"").decode())
+    return out
 
 
 def _check(rc, handle):
