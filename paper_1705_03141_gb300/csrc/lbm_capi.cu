@@ -282,11 +282,7 @@ lbm_status lbm_create(int nx, int ny, int nz, const lbm_params* p, lbm** out) {
   P.force_mode = p->force_mode;
   P.rho_ref = p->force_mode == LBM_FORCE_BUOYANCY ? 0.5 * (p->rho_r0 + p->rho_b0) : p->rho_b0;
   P.seed = p->seed;
-  for (int t = 0; t < 27; ++t) {
-    const double w = lbmk::weight_of(t);
-    P.refR[t] = p->rho_r0 * (t == lbmk::REST ? P.alpha_r : 27.0 / 19.0 * (1.0 - P.alpha_r) * w);
-    P.refB[t] = p->rho_b0 * (t == lbmk::REST ? P.alpha_b : 27.0 / 19.0 * (1.0 - P.alpha_b) * w);
-  }
+
 
   if (p->workspace) {
     if (p->workspace_bytes < h->L.total) {

@@ -48,6 +48,7 @@ struct Geom {
   double xc, yc, r2;
 };
 
+// Host-side physical parameters (FP64); converted to KConst<R> for the kernels.
 struct Phys {
   double rho_r0, rho_b0, alpha_r, alpha_b;
   double nu_r, nu_b, A, beta;
@@ -58,10 +59,66 @@ struct Phys {
   double rho_ref;   // reference density of the force mode
   double u_j0, noise_frac;
   uint64_t seed;
-  double refR[27], refB[27];  // packed storage: rest-state value of each direction in pure red / blue
 };
 
-__device__ __forceinline__ bool is_shear_moment(int j) { return j >= 5 && j <= 9; }  // slots s6, s8
+// Kernel constants in the compute type R (FP32 kernels read float constants:
+// no conversion in the inner loops).
+template <typename R>
+struct KConst {
+  R alpha_r, alpha_b;
+  R crest_r, crest_b;      // (27/19)(1 - alpha_k): varphi_i^k = crest_k w_i for moving i
+  R nu_mid, nu_half;       // nu_bar = nu_mid + nu_half * phi
+  R a_mid, a_half;         // alpha_bar = a_mid + a_half * phi
+  R A, beta;
+  R kd[27];
+  R invd[27];
+  R g[3];
+  R rho_ref;
+  int force_mode;
+  // packed storage: rest-state value of a direction of speed class s (|c|^2 = s)
+  // at red fraction q is refB[s] + q * dref[s]; dref is zero for moving classes.
+  R refB[4], dref[4];
+  // inlet (noise in FP64 so that both precisions draw the same variates)
+  double rho_r0_d, alpha_r_d, u_j0, noise_frac;
+  uint64_t seed;
+};
+
+template <typename R>
+inline KConst<R> make_kconst(const Phys& P) {
+  KConst<R> K;
+  K.alpha_r = (R)P.alpha_r;
+  K.alpha_b = (R)P.alpha_b;
+  K.crest_r = (R)(27.0 / 19.0 * (1.0 - P.alpha_r));
+  K.crest_b = (R)(27.0 / 19.0 * (1.0 - P.alpha_b));
+  K.nu_mid = (R)(0.5 * (P.nu_r + P.nu_b));
+  K.nu_half = (R)(0.5 * (P.nu_r - P.nu_b));
+  K.a_mid = (R)(0.5 * (P.alpha_r + P.alpha_b));
+  K.a_half = (R)(0.5 * (P.alpha_r - P.alpha_b));
+  K.A = (R)P.A;
+  K.beta = (R)P.beta;
+  for (int j = 0; j < 27; ++j) {
+    K.kd[j] = (R)P.kd[j];
+    K.invd[j] = (R)P.invd[j];
+  }
+  for (int a = 0; a < 3; ++a) K.g[a] = (R)P.g[a];
+  K.rho_ref = (R)P.rho_ref;
+  K.force_mode = P.force_mode;
+  const double wcls[4] = {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0};
+  for (int s = 0; s < 4; ++s) {
+    const double rb = P.rho_b0 * (s == 0 ? P.alpha_b : 27.0 / 19.0 * (1.0 - P.alpha_b) * wcls[s]);
+    const double rr = P.rho_r0 * (s == 0 ? P.alpha_r : 27.0 / 19.0 * (1.0 - P.alpha_r) * wcls[s]);
+    K.refB[s] = (R)rb;
+    K.dref[s] = (R)(s == 0 ? rr - rb : 0.0);  // equal for moving classes (gamma = (1-alpha_b)/(1-alpha_r))
+  }
+  K.rho_r0_d = P.rho_r0;
+  K.alpha_r_d = P.alpha_r;
+  K.u_j0 = P.u_j0;
+  K.noise_frac = P.noise_frac;
+  K.seed = P.seed;
+  return K;
+}
+
+__host__ __device__ __forceinline__ bool is_shear_moment(int j) { return j >= 5 && j <= 9; }  // slots s6, s8
 
 __host__ __device__ __forceinline__ int64_t snode(const Geom& g, int x, int y, int z) {
   return (int64_t)x + (int64_t)g.nx * ((int64_t)y + (int64_t)g.ny * (int64_t)(z + 1));
@@ -74,6 +131,14 @@ __device__ __forceinline__ bool is_inlet(const Geom& g, int x, int y, int z) {
   double dx = x - g.xc, dy = y - g.yc;
   return dx * dx + dy * dy < g.r2;
 }
+
+// fast reciprocal / inverse square root: exact in FP64 (oracle parity), MUFU in FP32
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double sat_(double x) { return fmin(fmax(x, 0.0), 1.0); }
+__device__ __forceinline__ float sat_(float x) { return __saturatef(x); }
 
 // Per-node streaming map: for each axis and side the node-index offset of the
 // neighbour, whether that side reflects the component (free-slip) and whether
@@ -126,73 +191,6 @@ struct NodeMap {
   }
 };
 
-// ---------------------------------------------------------------------------
-// storage policies
-
-template <typename T>
-struct PlainStore {  // FP64 or FP32: f^r and f^b planes [2][27][Ns]
-  T* A;
-  int64_t Ns;
-  template <typename R>
-  __device__ __forceinline__ void load(int64_t node, int dir, const Phys&, R& fr, R& fb) const {
-    fr = (R)__ldcs(A + (int64_t)dir * Ns + node);
-    fb = (R)__ldcs(A + (int64_t)(27 + dir) * Ns + node);
-  }
-  template <typename R>
-  __device__ __forceinline__ void store(int64_t node, int dir, const Phys&, R fr, R fb, R) const {
-    __stcs(A + (int64_t)dir * Ns + node, (T)fr);
-    __stcs(A + (int64_t)(27 + dir) * Ns + node, (T)fb);
-  }
-};
-
-// Packed 16+16 bit storage: per direction and node one 32-bit word holding
-// the total population's deviation from its rest-state value (IEEE half or
-// bfloat16, low half) and the red fraction q = f^r/f (unsigned 16-bit fixed
-// point, high half, exact 0 and 1).  The rest-state value of direction i is
-// q*rho_r0*varphi_i(alpha_r) + (1-q)*rho_b0*w_i, the population of a fluid at
-// rest with red fraction q; for i != rest both terms coincide by the density
-// ratio relation gamma = (1-alpha_b)/(1-alpha_r) of Sec. II.
-template <bool BF16>
-struct PackedStore {
-  uint32_t* A;
-  int64_t Ns;
-  __device__ __forceinline__ static float dev_to_float(uint32_t bits) {
-    if (BF16) return __bfloat162float(__ushort_as_bfloat16((unsigned short)(bits & 0xFFFFu)));
-    return __half2float(__ushort_as_half((unsigned short)(bits & 0xFFFFu)));
-  }
-  __device__ __forceinline__ static uint32_t float_to_dev(float v) {
-    if (BF16) return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v));
-    return (uint32_t)__half_as_ushort(__float2half_rn(v));
-  }
-  template <typename R>
-  __device__ __forceinline__ void load(int64_t node, int dir, const Phys& P, R& fr, R& fb) const {
-    const uint32_t w = __ldcs(A + (int64_t)dir * Ns + node);
-    const float q = (float)(w >> 16) * (1.0f / 65535.0f);
-    const float ref = (float)P.refB[dir] + q * (float)(P.refR[dir] - P.refB[dir]);
-    const float f = ref + dev_to_float(w);
-    const float r = q * f;
-    fr = (R)r;
-    fb = (R)(f - r);
-  }
-  // q_fallback: red fraction used when the total population is too small
-  // for f^r/f to mean anything (the node's rho_r/rho).
-  template <typename R>
-  __device__ __forceinline__ void store(int64_t node, int dir, const Phys& P, R fr, R fb, R q_fallback) const {
-    const float f = (float)fr + (float)fb;
-    float q = f > 1e-6f ? (float)fr / f : (float)q_fallback;
-    q = fminf(fmaxf(q, 0.0f), 1.0f);
-    const uint32_t qb = (uint32_t)__float2uint_rn(q * 65535.0f);
-    const float qq = (float)qb * (1.0f / 65535.0f);
-    const float ref = (float)P.refB[dir] + qq * (float)(P.refR[dir] - P.refB[dir]);
-    __stcs(A + (int64_t)dir * Ns + node, (qb << 16) | float_to_dev(f - ref));
-  }
-};
-
-template <class Store>
-struct DensOf { using type = float2; using real = float; };
-template <>
-struct DensOf<PlainStore<double>> { using type = double2; using real = double; };
-
 // slot holding the post-streaming population (x, t) in a layout (runtime t)
 __device__ __forceinline__ void slot_of(const NodeMap& nm, int layout, int t, int64_t& node, int& dir) {
   if (layout == 0) {
@@ -212,201 +210,275 @@ __device__ __forceinline__ void slot_of(const NodeMap& nm, int layout, int t, in
 }
 
 // ---------------------------------------------------------------------------
+// storage policies.  `cls` is the speed class |c|^2 of the direction; it is
+// unchanged by reflection and bounce-back, so the hot kernels pass it as a
+// compile-time value even when the slot's direction index is a runtime value.
+
+template <typename T>
+struct PlainStore {  // FP64 or FP32: f^r and f^b planes [2][27][Ns]
+  using real = T;
+  T* A;
+  int64_t Ns;
+  template <typename R>
+  __device__ __forceinline__ void load(int64_t node, int dir, int, const KConst<R>&, R& fr, R& fb) const {
+    fr = (R)__ldcs(A + (int64_t)dir * Ns + node);
+    fb = (R)__ldcs(A + (int64_t)(27 + dir) * Ns + node);
+  }
+  // outr, outb: the two colours; fstar = outr + outb and q = outr / fstar are for packed storage
+  template <typename R>
+  __device__ __forceinline__ void store(int64_t node, int dir, int, const KConst<R>&, R outr, R outb, R, R) const {
+    __stcs(A + (int64_t)dir * Ns + node, (T)outr);
+    __stcs(A + (int64_t)(27 + dir) * Ns + node, (T)outb);
+  }
+};
+
+// Packed 16+16 bit storage: per direction and node one 32-bit word holding
+// the total population's deviation from its rest-state value (IEEE half or
+// bfloat16, low half) and the red fraction q = f^r/f (unsigned 16-bit fixed
+// point, high half, exact 0 and 1).  The rest-state value of a direction is
+// q*rho_r0*varphi_i(alpha_r) + (1-q)*rho_b0*w_i, the population of a fluid at
+// rest with red fraction q; for moving directions both terms coincide by the
+// density ratio relation gamma = (1-alpha_b)/(1-alpha_r) of Sec. II.
+template <bool BF16>
+struct PackedStore {
+  using real = float;
+  uint32_t* A;
+  int64_t Ns;
+  __device__ __forceinline__ static float dev_to_float(uint32_t bits) {
+    if (BF16) return __uint_as_float(bits << 16);
+    return __half2float(__ushort_as_half((unsigned short)(bits & 0xFFFFu)));
+  }
+  __device__ __forceinline__ static uint32_t float_to_dev(float v) {
+    if (BF16) return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v));
+    return (uint32_t)__half_as_ushort(__float2half_rn(v));
+  }
+  // 16-bit code k -> k as a float, exactly, through the 2^23 magic number
+  __device__ __forceinline__ static float code_to_float(uint32_t k) {
+    return __uint_as_float(0x4B000000u | k) - 8388608.0f;
+  }
+  template <typename R>
+  __device__ __forceinline__ void load(int64_t node, int dir, int cls, const KConst<R>& K, R& fr, R& fb) const {
+    const uint32_t w = __ldcs(A + (int64_t)dir * Ns + node);
+    const float q = code_to_float(w >> 16) * (1.0f / 65535.0f);
+    const float f = fmaf(q, (float)K.dref[cls], (float)K.refB[cls]) + dev_to_float(w);
+    const float r = q * f;
+    fr = (R)r;
+    fb = (R)(f - r);
+  }
+  template <typename R>
+  __device__ __forceinline__ void store(int64_t node, int dir, int cls, const KConst<R>& K, R, R, R fstar,
+                                        R q) const {
+    const float qk = fmaf(__saturatef((float)q), 65535.0f, 8388608.0f);  // rounds to the nearest code
+    const uint32_t k = __float_as_uint(qk) & 0xFFFFu;
+    const float qq = (qk - 8388608.0f) * (1.0f / 65535.0f);
+    const float ref = fmaf(qq, (float)K.dref[cls], (float)K.refB[cls]);
+    __stcs(A + (int64_t)dir * Ns + node, (k << 16) | float_to_dev((float)fstar - ref));
+  }
+};
+
+template <class Store>
+struct DensOf { using type = float2; using real = float; };
+template <>
+struct DensOf<PlainStore<double>> { using type = double2; using real = double; };
+
+// ---------------------------------------------------------------------------
 // load all 27 x 2 populations of a node with the layout of the step about to run
 template <class Store, typename R>
-__device__ __forceinline__ void load_node(const Store& st, const Phys& P, const NodeMap& nm, int layout,
+__device__ __forceinline__ void load_node(const Store& st, const KConst<R>& K, const NodeMap& nm, int layout,
                                           R fr[27], R fb[27]) {
   if (layout == 0) {
 #pragma unroll
-    for (int t = 0; t < 27; ++t) st.load(nm.base, t, P, fr[t], fb[t]);
+    for (int t = 0; t < 27; ++t) st.load(nm.base, t, speed2_of(t), K, fr[t], fb[t]);
   } else {
 #pragma unroll
     for (int t = 0; t < 27; ++t) {
       int64_t node;
       int dir;
-      switch (26 - t) {  // read slot S(x, opp(t))
-#define LBMK_CASE(k) case k: nm.push<k>(node, dir); break;
-        LBMK_CASE(0) LBMK_CASE(1) LBMK_CASE(2) LBMK_CASE(3) LBMK_CASE(4) LBMK_CASE(5) LBMK_CASE(6)
-        LBMK_CASE(7) LBMK_CASE(8) LBMK_CASE(9) LBMK_CASE(10) LBMK_CASE(11) LBMK_CASE(12) LBMK_CASE(13)
-        LBMK_CASE(14) LBMK_CASE(15) LBMK_CASE(16) LBMK_CASE(17) LBMK_CASE(18) LBMK_CASE(19) LBMK_CASE(20)
-        LBMK_CASE(21) LBMK_CASE(22) LBMK_CASE(23) LBMK_CASE(24) LBMK_CASE(25) LBMK_CASE(26)
-#undef LBMK_CASE
-      }
-      st.load(node, dir, P, fr[t], fb[t]);
+      slot_of(nm, 1, t, node, dir);
+      st.load(node, dir, speed2_of(t), K, fr[t], fb[t]);
     }
   }
 }
 
-// write the post-collision value of direction t of a node (step parity `odd`)
-template <int T, class Store, typename R>
-__device__ __forceinline__ void emit(const Store& st, const Phys& P, const NodeMap& nm, bool odd, R fr, R fb, R qf) {
-  if (!odd) {
-    st.store(nm.base, opp_of(T), P, fr, fb, qf);
-  } else {
-    int64_t node;
-    int dir;
-    nm.push<T>(node, dir);
-    st.store(node, dir, P, fr, fb, qf);
-  }
-}
-
-template <int T, class Store, typename R>
-struct EmitLoop {
-  __device__ __forceinline__ static void run(const Store& st, const Phys& P, const NodeMap& nm, bool odd,
-                                             const R* fr, const R* fb, R qf) {
-    emit<T>(st, P, nm, odd, fr[T], fb[T], qf);
-    EmitLoop<T + 1, Store, R>::run(st, P, nm, odd, fr, fb, qf);
-  }
-};
-template <class Store, typename R>
-struct EmitLoop<27, Store, R> {
-  __device__ __forceinline__ static void run(const Store&, const Phys&, const NodeMap&, bool, const R*, const R*, R) {}
-};
-
-// ---------------------------------------------------------------------------
 // body force (Eq. Momentum / Eq. ketFd)
 template <typename R>
-__device__ __forceinline__ void body_force(const Phys& P, R rho, R F[3]) {
+__device__ __forceinline__ void body_force(const KConst<R>& K, R rho, R F[3]) {
   R k = R(0);
-  if (P.force_mode == FORCE_BUOYANCY || P.force_mode == FORCE_DISPERSED) k = rho - (R)P.rho_ref;
-  else if (P.force_mode == FORCE_UNIFORM) k = R(1);
-  F[0] = k * (R)P.g[0];
-  F[1] = k * (R)P.g[1];
-  F[2] = k * (R)P.g[2];
+  if (K.force_mode == FORCE_BUOYANCY || K.force_mode == FORCE_DISPERSED) k = rho - K.rho_ref;
+  else if (K.force_mode == FORCE_UNIFORM) k = R(1);
+  F[0] = k * K.g[0];
+  F[1] = k * K.g[1];
+  F[2] = k * K.g[2];
 }
 
-// Collision of one node, in place: fr/fb (post-streaming, in) become the
-// recoloured post-collision values (out).  gphi, grho: isotropic gradients of
-// phi and rho.  Returns rho_r/rho in *qf.
-//
-//   f = f^r + f^b; the operators are linear in the colours, so the MRT step
-//   acts on the total f with the total equilibrium
-//     f^(e)_i = sum_k rho_k varphi_i^k + rho w_i [3 c.u + 9/2 (c.u)^2 - 3/2 u^2] + Phi_i,
-//   Phi_i = 9 w_i nu_bar (c.u)(c.grad rho) (i != rest), -3 nu_bar u.grad rho (rest)
-//   (Eq. EES, Eq. varphi_ik, Eq. Phi summed over k; 16/4/1 divided by 48/2 = 9 w_i),
-//   and f* = f - M^-1 K M (f - f^(e) + F'/2) + F' + Omega^(2)   (Eq. scoll, Eq. ketF),
-//   F'_i = w_i [3 (c - u) + 9 (c.u) c].F (Eq. ketFd),
-//   Omega^(2)_i = A |grad phi| [w_i (c.n)^2 - B_i] with B_i = w_i (i != rest),
-//   -10/27 (rest) (Eq. perturb with the square, Eq. B_i; A_r = A_b = A),
-//   then recolouring: f^r_i = (rho_r/rho) f*_i + beta rho_r rho_b/rho varphi_i(alpha_bar) cos(theta_i).
+// What the recolouring needs per node after the collision.
 template <typename R>
-__device__ __forceinline__ void collide(const Phys& P, R fr[27], R fb[27], const R gphi[3], const R grho[3], R* qf) {
-  R rho_r = R(0), rho_b = R(0);
+struct Recol {
+  R frac;        // rho_r / rho
+  R n0, n1, n2;  // unit normal grad(phi)/|grad(phi)| (0 where undefined)
+  R rc[4];       // beta rho_r rho_b / rho * varphi_i(alpha_bar) / |c_i| per speed class (rc[0] unused)
+  bool has_n;
+};
+
+// Collision of one node.  fr/fb: post-streaming populations (in).  On return
+// f[t] holds f*_t, the total post-collision population including forcing and
+// perturbation, and the returned Recol splits it into colours:
+//   f^r_t = frac f*_t + rc[|c_t|^2] (c_t . n),   f^b_t = f*_t - f^r_t.
+//
+// The operators are linear in the colours, so the MRT step acts on the total f
+// (R4).  With the total equilibrium of Eq. (EES) summed over k and the
+// forcing of Eq. (ketFd),
+//   h_i = f_i - f^(e)_i + F'_i/2 = f_i - w_i Q(c_i) - delta_{i,rest} E,
+//   Q(c) = C0 + c.V + c.S.c,   C0 = P - 3/2 rho u^2 + 3/2 u.F,   V = 3 rho u - 3/2 F,
+//   S = 9/2 rho u u + 9/2 nu_bar (u g + g u) - 9/4 (u F + F u),
+//   E = sum_k rho_k alpha_k - w_rest P - 3 nu_bar u.g,   P = sum_k rho_k crest_k,
+// (g = grad rho; Phi_i = 9 w_i nu_bar (c.u)(c.g) for moving i, Eq. Phi with
+// 16/4/1 / 48 * 2 = 9 w_i).  The raw moments of w_i c^p are products of the
+// D1Q3 weight moments (1, 0, 1/3), so the raw moments of h are those of f
+// (one cascade) minus closed forms.  Then f* = f + M^-1(-K M h) + F' + Omega^(2)
+// with M^-1 = M^T diag(1/|M_j|^2) (Eq. scoll, Eq. ketF), and
+// Omega^(2)_i = A |grad phi| [w_i (c.n)^2 - B_i], B_i = w_i for moving i and
+// -10/27 at rest (Eq. perturb with the square, R1; Eq. B_i).
+template <typename R>
+__device__ __forceinline__ Recol<R> collide(const KConst<R>& K, const R fr[27], const R fb[27], const R gphi[3],
+                                            const R grho[3], R f[27]) {
+  R rho_r = R(0);
+#pragma unroll
+  for (int t = 0; t < 27; ++t) rho_r += fr[t];
+  R r[27];
 #pragma unroll
   for (int t = 0; t < 27; ++t) {
-    rho_r += fr[t];
-    rho_b += fb[t];
+    f[t] = fr[t] + fb[t];
+    r[t] = f[t];
   }
-  R f[27];
-#pragma unroll
-  for (int t = 0; t < 27; ++t) f[t] = fr[t] + fb[t];
-  const R rho = rho_r + rho_b;
-  const R inv_rho = R(1) / rho;
-  const R phi = (rho_r - rho_b) * inv_rho;
-  R j0 = R(0), j1 = R(0), j2 = R(0);
-#pragma unroll
-  for (int t = 0; t < 27; ++t) {
-    if (cx_of(t) > 0) j0 += f[t];
-    if (cx_of(t) < 0) j0 -= f[t];
-    if (cy_of(t) > 0) j1 += f[t];
-    if (cy_of(t) < 0) j1 -= f[t];
-    if (cz_of(t) > 0) j2 += f[t];
-    if (cz_of(t) < 0) j2 -= f[t];
-  }
+  raw_forward(r);
+  const R rho = r[0];
+  const R rho_b = rho - rho_r;
+  const R inv_rho = rcp_(rho);
   R F[3];
-  body_force(P, rho, F);
-  const R u0 = (j0 + R(0.5) * F[0]) * inv_rho;
-  const R u1 = (j1 + R(0.5) * F[1]) * inv_rho;
-  const R u2 = (j2 + R(0.5) * F[2]) * inv_rho;
-  const R ar = (R)P.alpha_r, ab = (R)P.alpha_b;
-  const R nubar = R(0.5) * ((R(1) + phi) * (R)P.nu_r + (R(1) - phi) * (R)P.nu_b);
-  const R s_sh = R(1) / (R(3) * nubar + R(0.5));
-  const R prest = R(27.0 / 19.0) * (rho_r * (R(1) - ar) + rho_b * (R(1) - ab));
-  const R rest0 = rho_r * ar + rho_b * ab;
+  body_force(K, rho, F);
+  const R u0 = (r[1] + R(0.5) * F[0]) * inv_rho;
+  const R u1 = (r[3] + R(0.5) * F[1]) * inv_rho;
+  const R u2 = (r[9] + R(0.5) * F[2]) * inv_rho;
+  const R phi = (rho_r - rho_b) * inv_rho;
+  const R nubar = K.nu_mid + K.nu_half * phi;
+  const R s_sh = rcp_(R(3) * nubar + R(0.5));
+  const R Pr = K.crest_r * rho_r + K.crest_b * rho_b;
+  const R g0 = grho[0], g1 = grho[1], g2 = grho[2];
   const R uu = u0 * u0 + u1 * u1 + u2 * u2;
   const R uF = u0 * F[0] + u1 * F[1] + u2 * F[2];
-  const R ug = u0 * grho[0] + u1 * grho[1] + u2 * grho[2];
 
-  // h = f - f^(e) + F'/2, then its moments
-  R h[27];
-#pragma unroll
-  for (int t = 0; t < 27; ++t) {
-    const R w = (R)weight_of(t);
-    if (t == REST) {
-      const R feq = rest0 - w * R(1.5) * rho * uu - R(3) * nubar * ug;
-      h[t] = f[t] - feq - R(1.5) * w * uF;
-    } else {
-      const R cu = R(cx_of(t)) * u0 + R(cy_of(t)) * u1 + R(cz_of(t)) * u2;
-      const R cg = R(cx_of(t)) * grho[0] + R(cy_of(t)) * grho[1] + R(cz_of(t)) * grho[2];
-      const R cF = R(cx_of(t)) * F[0] + R(cy_of(t)) * F[1] + R(cz_of(t)) * F[2];
-      const R feq = w * (prest + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu) + R(9) * nubar * cu * cg);
-      const R fp = w * (R(3) * cF - R(3) * uF + R(9) * cu * cF);
-      h[t] = f[t] - feq + R(0.5) * fp;
-    }
-  }
-  raw_forward(h);
+  // closed-form raw moments of w_i Q(c_i), subtracted from those of f
+  // (delta_rest E only enters R000, which is set to its exact value 0)
+  const R C0 = Pr - R(1.5) * rho * uu + R(1.5) * uF;
+  const R V0 = R(3) * rho * u0 - R(1.5) * F[0];
+  const R V1 = R(3) * rho * u1 - R(1.5) * F[1];
+  const R V2 = R(3) * rho * u2 - R(1.5) * F[2];
+  const R r45 = R(4.5) * rho, n45 = R(4.5) * nubar;
+  const R Sxx = r45 * u0 * u0 + R(2) * n45 * u0 * g0 - R(4.5) * u0 * F[0];
+  const R Syy = r45 * u1 * u1 + R(2) * n45 * u1 * g1 - R(4.5) * u1 * F[1];
+  const R Szz = r45 * u2 * u2 + R(2) * n45 * u2 * g2 - R(4.5) * u2 * F[2];
+  const R Sxy = r45 * u0 * u1 + n45 * (u0 * g1 + u1 * g0) - R(2.25) * (u0 * F[1] + u1 * F[0]);
+  const R Syz = r45 * u1 * u2 + n45 * (u1 * g2 + u2 * g1) - R(2.25) * (u1 * F[2] + u2 * F[1]);
+  const R Sxz = r45 * u0 * u2 + n45 * (u0 * g2 + u2 * g0) - R(2.25) * (u0 * F[2] + u2 * F[0]);
+  const R t3 = R(1.0 / 3.0), t9 = R(1.0 / 9.0), t27 = R(1.0 / 27.0);
+#define LBMK_IX(a, b, c) ((a) + 3 * (b) + 9 * (c))
+  // mass and momentum of h vanish identically (conserved by the equilibrium with the F/2 shift)
+  r[LBMK_IX(0, 0, 0)] = R(0);
+  r[LBMK_IX(1, 0, 0)] = R(0);
+  r[LBMK_IX(0, 1, 0)] = R(0);
+  r[LBMK_IX(0, 0, 1)] = R(0);
+  r[LBMK_IX(2, 0, 0)] -= t3 * (C0 + Sxx) + t9 * (Syy + Szz);
+  r[LBMK_IX(0, 2, 0)] -= t3 * (C0 + Syy) + t9 * (Sxx + Szz);
+  r[LBMK_IX(0, 0, 2)] -= t3 * (C0 + Szz) + t9 * (Sxx + Syy);
+  r[LBMK_IX(2, 2, 0)] -= t9 * (C0 + Sxx + Syy) + t27 * Szz;
+  r[LBMK_IX(2, 0, 2)] -= t9 * (C0 + Sxx + Szz) + t27 * Syy;
+  r[LBMK_IX(0, 2, 2)] -= t9 * (C0 + Syy + Szz) + t27 * Sxx;
+  r[LBMK_IX(2, 2, 2)] -= t27 * (C0 + Sxx + Syy + Szz);
+  r[LBMK_IX(1, 2, 0)] -= t9 * V0;
+  r[LBMK_IX(1, 0, 2)] -= t9 * V0;
+  r[LBMK_IX(1, 2, 2)] -= t27 * V0;
+  r[LBMK_IX(2, 1, 0)] -= t9 * V1;
+  r[LBMK_IX(0, 1, 2)] -= t9 * V1;
+  r[LBMK_IX(2, 1, 2)] -= t27 * V1;
+  r[LBMK_IX(2, 0, 1)] -= t9 * V2;
+  r[LBMK_IX(0, 2, 1)] -= t9 * V2;
+  r[LBMK_IX(2, 2, 1)] -= t27 * V2;
+  r[LBMK_IX(1, 1, 0)] -= R(2) * t9 * Sxy;
+  r[LBMK_IX(1, 1, 2)] -= R(2) * t27 * Sxy;
+  r[LBMK_IX(0, 1, 1)] -= R(2) * t9 * Syz;
+  r[LBMK_IX(2, 1, 1)] -= R(2) * t27 * Syz;
+  r[LBMK_IX(1, 0, 1)] -= R(2) * t9 * Sxz;
+  r[LBMK_IX(1, 2, 1)] -= R(2) * t27 * Sxz;
+  // R111 of w Q is zero
+#undef LBMK_IX
+
   R m[27];
-  moment_forward(h, m);
+  moment_forward(r, m);
   R y[27];
 #pragma unroll
   for (int j = 0; j < 4; ++j) y[j] = R(0);
 #pragma unroll
-  for (int j = 4; j < 27; ++j) y[j] = -(is_shear_moment(j) ? s_sh * (R)P.invd[j] : (R)P.kd[j]) * m[j];
-  R r[27];
+  for (int j = 4; j < 27; ++j) y[j] = -(is_shear_moment(j) ? s_sh * K.invd[j] : K.kd[j]) * m[j];
   moment_adjoint(y, r);
   raw_adjoint(r);
 
-  // perturbation and recolouring
-  const R g2 = gphi[0] * gphi[0] + gphi[1] * gphi[1] + gphi[2] * gphi[2];
-  const bool has_n = g2 > R(1e-24);
-  const R gn = has_n ? sqrt(g2) : R(0);
-  const R inv_gn = has_n ? R(1) / gn : R(0);
-  const R n0 = gphi[0] * inv_gn, n1 = gphi[1] * inv_gn, n2 = gphi[2] * inv_gn;
-  const R Ag = (R)P.A * gn;
-  const R abar = R(0.5) * ((R(1) + phi) * ar + (R(1) - phi) * ab);
-  const R rec = (R)P.beta * rho_r * rho_b * inv_rho;
-  const R frac = rho_r * inv_rho;
+  // perturbation and recolouring scalars
+  Recol<R> out;
+  const R G0 = gphi[0], G1 = gphi[1], G2 = gphi[2];
+  const R gg = G0 * G0 + G1 * G1 + G2 * G2;
+  out.has_n = gg > R(1e-24);
+  const R inv_gn = out.has_n ? rsqrt_(gg) : R(0);
+  out.n0 = G0 * inv_gn;
+  out.n1 = G1 * inv_gn;
+  out.n2 = G2 * inv_gn;
+  const R Ag = K.A * gg * inv_gn;  // A |grad phi|
+  const R abar = K.a_mid + K.a_half * phi;
+  const R cr = K.beta * rho_r * rho_b * inv_rho * R(27.0 / 19.0) * (R(1) - abar);
+  out.frac = rho_r * inv_rho;
+  out.rc[0] = R(0);
+  out.rc[1] = cr * R(weight_of(tensor_index(1, 0, 0)));
+  out.rc[2] = cr * R(weight_of(tensor_index(1, 1, 0)) * 0.70710678118654752440);
+  out.rc[3] = cr * R(weight_of(tensor_index(1, 1, 1)) * 0.57735026918962576451);
+  const R Aw1 = Ag * R(weight_of(tensor_index(1, 0, 0)));
+  const R Aw2 = Ag * R(weight_of(tensor_index(1, 1, 0)));
+  const R Aw3 = Ag * R(weight_of(tensor_index(1, 1, 1)));
+  const R uF3 = R(3) * uF;
+
 #pragma unroll
   for (int t = 0; t < 27; ++t) {
-    const R w = (R)weight_of(t);
-    R fstar, rc;
     if (t == REST) {
-      fstar = f[t] + r[t] - R(3) * w * uF + Ag * R(10.0 / 27.0);
-      rc = R(0);
+      f[t] = f[t] + r[t] - R(weight_of(REST)) * uF3 + Ag * R(10.0 / 27.0);
     } else {
+      const R w = R(weight_of(t));
       const R cu = R(cx_of(t)) * u0 + R(cy_of(t)) * u1 + R(cz_of(t)) * u2;
       const R cF = R(cx_of(t)) * F[0] + R(cy_of(t)) * F[1] + R(cz_of(t)) * F[2];
-      const R cn = R(cx_of(t)) * n0 + R(cy_of(t)) * n1 + R(cz_of(t)) * n2;
-      const R fp = w * (R(3) * cF - R(3) * uF + R(9) * cu * cF);
-      fstar = f[t] + r[t] + fp + Ag * w * (cn * cn - R(1));
-      const R inv_speed = speed2_of(t) == 1 ? R(1) : (speed2_of(t) == 2 ? R(0.70710678118654752440) : R(0.57735026918962576451));
-      rc = rec * R(27.0 / 19.0) * (R(1) - abar) * w * cn * inv_speed;
+      const R cn = R(cx_of(t)) * out.n0 + R(cy_of(t)) * out.n1 + R(cz_of(t)) * out.n2;
+      const R Aw = speed2_of(t) == 1 ? Aw1 : (speed2_of(t) == 2 ? Aw2 : Aw3);
+      const R fp = (R(9) * w * cu) * cF + w * (R(3) * cF - uF3);  // F'_t (Eq. ketFd)
+      f[t] = f[t] + r[t] + fp + (Aw * cn * cn - Aw);
     }
-    const R outr = frac * fstar + rc;
-    fr[t] = outr;
-    fb[t] = fstar - outr;
   }
-  *qf = frac;
+  return out;
 }
 
 // Dirichlet inlet node (Sec. IV.A): f^r = f^{r(e)}(rho_r0, u_in, alpha_r) with Phi = 0, f^b = 0.
 template <typename R>
-__device__ __forceinline__ void inlet_state(const Phys& P, int64_t node_lin, int64_t step, R fr[27], R fb[27]) {
-  double u[3] = {0.0, 0.0, P.u_j0};
-  if (P.noise_frac != 0.0) {
+__device__ __forceinline__ void inlet_state(const KConst<R>& K, int64_t node_lin, int64_t step, R f[27]) {
+  double u[3] = {0.0, 0.0, K.u_j0};
+  if (K.noise_frac != 0.0) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) u[a] += P.u_j0 * P.noise_frac * inlet_noise(P.seed, step, node_lin, a);
+    for (int a = 0; a < 3; ++a) u[a] += K.u_j0 * K.noise_frac * inlet_noise(K.seed, step, node_lin, a);
   }
   const R u0 = (R)u[0], u1 = (R)u[1], u2 = (R)u[2];
-  const R rho = (R)P.rho_r0, ar = (R)P.alpha_r;
+  const R rho = (R)K.rho_r0_d, ar = (R)K.alpha_r_d;
   const R uu = u0 * u0 + u1 * u1 + u2 * u2;
 #pragma unroll
   for (int t = 0; t < 27; ++t) {
     const R w = (R)weight_of(t);
     const R cu = R(cx_of(t)) * u0 + R(cy_of(t)) * u1 + R(cz_of(t)) * u2;
     const R vphi = t == REST ? ar : R(27.0 / 19.0) * (R(1) - ar) * w;
-    fr[t] = rho * (vphi + w * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));
-    fb[t] = R(0);
+    f[t] = rho * (vphi + w * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));
   }
 }
 
@@ -416,11 +488,52 @@ __device__ __forceinline__ int wrap_or_clamp(int q, int n, int bc_lo, int bc_hi)
   return q;
 }
 
+// write direction T of the node (step parity `odd`): colours, f* and red fraction
+template <int T, class Store, typename R>
+__device__ __forceinline__ void emit(const Store& st, const KConst<R>& K, const NodeMap& nm, bool odd, const R f[27],
+                                     const Recol<R>& rc) {
+  const R fstar = f[T];
+  R outr, q;
+  if (T == REST) {
+    outr = rc.frac * fstar;
+    q = rc.frac;
+  } else {
+    const R cn = R(cx_of(T)) * rc.n0 + R(cy_of(T)) * rc.n1 + R(cz_of(T)) * rc.n2;
+    const R rcol = rc.rc[speed2_of(T)] * cn;
+    outr = rc.frac * fstar + rcol;
+    q = rc.has_n ? sat_(outr * rcp_(fstar)) : rc.frac;
+  }
+  const R outb = fstar - outr;
+  if (!odd) {
+    st.store(nm.base, opp_of(T), speed2_of(T), K, outr, outb, fstar, q);
+  } else {
+    int64_t node;
+    int dir;
+    nm.push<T>(node, dir);
+    st.store(node, dir, speed2_of(T), K, outr, outb, fstar, q);
+  }
+}
+
+template <int T, class Store, typename R>
+struct EmitLoop {
+  __device__ __forceinline__ static void run(const Store& st, const KConst<R>& K, const NodeMap& nm, bool odd,
+                                             const R* f, const Recol<R>& rc) {
+    emit<T>(st, K, nm, odd, f, rc);
+    EmitLoop<T + 1, Store, R>::run(st, K, nm, odd, f, rc);
+  }
+};
+template <class Store, typename R>
+struct EmitLoop<27, Store, R> {
+  __device__ __forceinline__ static void run(const Store&, const KConst<R>&, const NodeMap&, bool, const R*,
+                                             const Recol<R>&) {}
+};
+
 // ---------------------------------------------------------------------------
 // pass 1: density / phase field
 template <class Store>
-__global__ void __launch_bounds__(NTHREADS) k_density(Store st, Geom G, Phys P, int layout,
-                                                      typename DensOf<Store>::type* __restrict__ dens,
+__global__ void __launch_bounds__(NTHREADS) k_density(Store st, Geom G,
+                                                      const __grid_constant__ KConst<typename DensOf<Store>::real> K,
+                                                      int layout, typename DensOf<Store>::type* __restrict__ dens,
                                                       int* __restrict__ flag, long long* __restrict__ step_counter) {
   using D = typename DensOf<Store>::real;
   // the counter holds the index of the step being taken (read by pass 2's inlet noise)
@@ -434,7 +547,7 @@ __global__ void __launch_bounds__(NTHREADS) k_density(Store st, Geom G, Phys P, 
   NodeMap nm;
   nm.init(G, x, y, z);
   D fr[27], fb[27];
-  load_node(st, P, nm, layout, fr, fb);
+  load_node(st, K, nm, layout, fr, fb);
   D rr = D(0), rb = D(0);
 #pragma unroll
   for (int t = 0; t < 27; ++t) {
@@ -442,7 +555,7 @@ __global__ void __launch_bounds__(NTHREADS) k_density(Store st, Geom G, Phys P, 
     rb += fb[t];
   }
   if (is_inlet(G, x, y, z)) {
-    rr = (D)P.rho_r0;
+    rr = (D)K.rho_r0_d;
     rb = D(0);
   }
   const D rho = rr + rb;
@@ -455,13 +568,12 @@ __global__ void __launch_bounds__(NTHREADS) k_density(Store st, Geom G, Phys P, 
 
 // pass 2: gradients + collision + perturbation + recolouring + in-place streaming
 template <class Store, int MINB>
-__global__ void __launch_bounds__(NTHREADS, MINB) k_collide_stream(Store st, const __grid_constant__ Geom G,
-                                                                   const __grid_constant__ Phys P, int odd,
-                                                                   const typename DensOf<Store>::type* __restrict__ dens,
-                                                                   const long long* __restrict__ step_counter) {
-  using D = typename DensOf<Store>::real;
+__global__ void __launch_bounds__(NTHREADS, MINB)
+    k_collide_stream(Store st, const __grid_constant__ Geom G,
+                     const __grid_constant__ KConst<typename DensOf<Store>::real> K, int odd,
+                     const typename DensOf<Store>::type* __restrict__ dens, const long long* __restrict__ step_counter) {
+  using R = typename DensOf<Store>::real;  // compute type: FP64 for FP64 storage, FP32 otherwise
   using DT = typename DensOf<Store>::type;
-  using R = D;  // compute type: FP64 for FP64 storage, FP32 otherwise
   __shared__ DT tile[TILE];
 
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * BZ;
@@ -472,7 +584,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_collide_stream(Store st, con
   R fr[27], fb[27];
   if (active) {
     nm.init(G, x, y, z);
-    load_node(st, P, nm, odd, fr, fb);
+    load_node(st, K, nm, odd, fr, fb);
   }
 
   const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
@@ -501,20 +613,33 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_collide_stream(Store st, con
     if (cz_of(t) != 0) { gphi[2] += R(cz_of(t)) * a; grho[2] += R(cz_of(t)) * b; }
   }
 
-  R qf;
+  R f[27];
+  Recol<R> rc;
   if (is_inlet(G, x, y, z)) {
-    inlet_state(P, dnode(G, x, y, z), (int64_t)*step_counter, fr, fb);
-    qf = R(1);
+    inlet_state(K, dnode(G, x, y, z), (int64_t)*step_counter, f);
+    rc.frac = R(1);
+    rc.n0 = rc.n1 = rc.n2 = R(0);
+    rc.rc[0] = rc.rc[1] = rc.rc[2] = rc.rc[3] = R(0);
+    rc.has_n = false;
   } else {
-    collide(P, fr, fb, gphi, grho, &qf);
+    rc = collide(K, fr, fb, gphi, grho, f);
   }
-  EmitLoop<0, Store, R>::run(st, P, nm, odd != 0, fr, fb, qf);
+  EmitLoop<0, Store, R>::run(st, K, nm, odd != 0, f, rc);
+}
+
+// write one population pair at (node, dir) of a runtime direction (I/O kernels)
+template <class Store, typename R>
+__device__ __forceinline__ void store_pair(const Store& st, const KConst<R>& K, int64_t node, int dir, R fr, R fb) {
+  const R s = fr + fb;
+  const R q = s > R(0) ? fr / s : R(0.5);
+  st.store(node, dir, speed2_of(dir), K, fr, fb, s, q);
 }
 
 // convective outflow on the z = nz-1 plane (Sec. IV.A), after the step that
 // produced time t+1; `layout` is the layout of time t+1.
 template <class Store>
-__global__ void k_outflow(Store st, Geom G, Phys P, int layout, typename DensOf<Store>::real* __restrict__ top) {
+__global__ void k_outflow(Store st, Geom G, const __grid_constant__ KConst<typename DensOf<Store>::real> K,
+                          int layout, typename DensOf<Store>::real* __restrict__ top) {
   using R = typename DensOf<Store>::real;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -525,7 +650,7 @@ __global__ void k_outflow(Store st, Geom G, Phys P, int layout, typename DensOf<
   below.init(G, x, y, G.nz - 2);
   here.init(G, x, y, G.nz - 1);
   R fr[27], fb[27];
-  load_node(st, P, below, layout, fr, fb);
+  load_node(st, K, below, layout, fr, fb);
   R rho = R(0), mz = R(0);
 #pragma unroll
   for (int t = 0; t < 27; ++t) {
@@ -535,7 +660,7 @@ __global__ void k_outflow(Store st, Geom G, Phys P, int layout, typename DensOf<
     if (cz_of(t) < 0) mz -= v;
   }
   R F[3];
-  body_force(P, rho, F);
+  body_force(K, rho, F);
   const R uz = (mz + R(0.5) * F[2]) / rho;
   const R lam = uz > R(0) ? uz : R(0);
   const R inv = R(1) / (R(1) + lam);
@@ -547,18 +672,10 @@ __global__ void k_outflow(Store st, Geom G, Phys P, int layout, typename DensOf<
     const R nb = (*tb + lam * fb[t]) * inv;
     *tr = nr;
     *tb = nb;
-    fr[t] = nr;
-    fb[t] = nb;
-  }
-  // write f(N, t+1) where the layout expects it
-#pragma unroll
-  for (int t = 0; t < 27; ++t) {
-    const R sum = fr[t] + fb[t];
-    const R qf = sum > R(0) ? fr[t] / sum : R(0.5);
     int64_t node;
     int dir;
     slot_of(here, layout, t, node, dir);
-    st.store(node, dir, P, fr[t], fb[t], qf);
+    store_pair(st, K, node, dir, nr, nb);
   }
 }
 
@@ -567,8 +684,8 @@ __global__ void k_outflow(Store st, Geom G, Phys P, int layout, typename DensOf<
 
 // f^k = f^{k(e)}(rho_k, u, alpha_k), Phi = 0; written in layout 0.
 template <class Store>
-__global__ void k_init(Store st, Geom G, Phys P, const double* __restrict__ rr, const double* __restrict__ rb,
-                       const double* __restrict__ u) {
+__global__ void k_init(Store st, Geom G, const __grid_constant__ KConst<typename DensOf<Store>::real> K,
+                       const double* __restrict__ rr, const double* __restrict__ rb, const double* __restrict__ u) {
   using R = typename DensOf<Store>::real;
   const int64_t N = (int64_t)G.nx * G.ny * G.nz;
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -577,23 +694,22 @@ __global__ void k_init(Store st, Geom G, Phys P, const double* __restrict__ rr, 
   const double u0 = u ? u[n] : 0.0, u1 = u ? u[N + n] : 0.0, u2 = u ? u[2 * N + n] : 0.0;
   const double uu = u0 * u0 + u1 * u1 + u2 * u2;
   const double r = rr[n], b = rb[n];
-  const double rho = r + b;
+  const double ar = K.alpha_r_d, ab = 8.0 / 27.0;
   const int64_t sn = snode(G, x, y, z);
   for (int t = 0; t < 27; ++t) {
     const double w = weight_of(t);
     const double cu = cx_of(t) * u0 + cy_of(t) * u1 + cz_of(t) * u2;
     const double poly = w * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-    const double vr = t == REST ? P.alpha_r : 27.0 / 19.0 * (1.0 - P.alpha_r) * w;
-    const double vb = t == REST ? P.alpha_b : 27.0 / 19.0 * (1.0 - P.alpha_b) * w;
-    const double er = r * (vr + poly), eb = b * (vb + poly);
-    st.store(sn, t, P, (R)er, (R)eb, (R)(rho > 0.0 ? r / rho : 0.5));
+    const double vr = t == REST ? ar : 27.0 / 19.0 * (1.0 - ar) * w;
+    const double vb = t == REST ? ab : 27.0 / 19.0 * (1.0 - ab) * w;
+    store_pair(st, K, sn, t, (R)(r * (vr + poly)), (R)(b * (vb + poly)));
   }
 }
 
 // one direction (paper order pdir) of the canonical [2][27][N] FP64 array <-> storage
 template <class Store>
-__global__ void k_get_pop(Store st, Geom G, Phys P, int layout, int pdir, double* __restrict__ out_r,
-                          double* __restrict__ out_b) {
+__global__ void k_get_pop(Store st, Geom G, const __grid_constant__ KConst<typename DensOf<Store>::real> K,
+                          int layout, int pdir, double* __restrict__ out_r, double* __restrict__ out_b) {
   using R = typename DensOf<Store>::real;
   const int64_t N = (int64_t)G.nx * G.ny * G.nz;
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -603,16 +719,17 @@ __global__ void k_get_pop(Store st, Geom G, Phys P, int layout, int pdir, double
   nm.init(G, x, y, z);
   int64_t node;
   int dir;
-  slot_of(nm, layout, paper_to_tensor(pdir), node, dir);
+  const int t = paper_to_tensor(pdir);
+  slot_of(nm, layout, t, node, dir);
   R fr, fb;
-  st.load(node, dir, P, fr, fb);
+  st.load(node, dir, speed2_of(t), K, fr, fb);
   out_r[n] = (double)fr;
   out_b[n] = (double)fb;
 }
 
 template <class Store>
-__global__ void k_set_pop(Store st, Geom G, Phys P, int layout, int pdir, const double* __restrict__ in_r,
-                          const double* __restrict__ in_b) {
+__global__ void k_set_pop(Store st, Geom G, const __grid_constant__ KConst<typename DensOf<Store>::real> K,
+                          int layout, int pdir, const double* __restrict__ in_r, const double* __restrict__ in_b) {
   using R = typename DensOf<Store>::real;
   const int64_t N = (int64_t)G.nx * G.ny * G.nz;
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -623,12 +740,13 @@ __global__ void k_set_pop(Store st, Geom G, Phys P, int layout, int pdir, const 
   int64_t node;
   int dir;
   slot_of(nm, layout, paper_to_tensor(pdir), node, dir);
-  st.store(node, dir, P, (R)in_r[n], (R)in_b[n], R(0.5));
+  store_pair(st, K, node, dir, (R)in_r[n], (R)in_b[n]);
 }
 
 // outflow history := the current populations of the z = nz-1 plane
 template <class Store>
-__global__ void k_top_from_state(Store st, Geom G, Phys P, int layout, typename DensOf<Store>::real* __restrict__ top) {
+__global__ void k_top_from_state(Store st, Geom G, const __grid_constant__ KConst<typename DensOf<Store>::real> K,
+                                 int layout, typename DensOf<Store>::real* __restrict__ top) {
   using R = typename DensOf<Store>::real;
   const int64_t Pn = (int64_t)G.nx * G.ny;
   const int64_t pp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -640,7 +758,7 @@ __global__ void k_top_from_state(Store st, Geom G, Phys P, int layout, typename 
     int dir;
     slot_of(nm, layout, t, node, dir);
     R fr, fb;
-    st.load(node, dir, P, fr, fb);
+    st.load(node, dir, speed2_of(t), K, fr, fb);
     top[(int64_t)t * Pn + pp] = fr;
     top[(int64_t)(27 + t) * Pn + pp] = fb;
   }
@@ -648,8 +766,8 @@ __global__ void k_top_from_state(Store st, Geom G, Phys P, int layout, typename 
 
 // rho_r, rho_b, u (Eq. Momentum) into FP64 device buffers (any may be null)
 template <class Store>
-__global__ void k_macro(Store st, Geom G, Phys P, int layout, double* __restrict__ rr, double* __restrict__ rb,
-                        double* __restrict__ u) {
+__global__ void k_macro(Store st, Geom G, const __grid_constant__ KConst<typename DensOf<Store>::real> K, int layout,
+                        double* __restrict__ rr, double* __restrict__ rb, double* __restrict__ u) {
   using R = typename DensOf<Store>::real;
   const int64_t N = (int64_t)G.nx * G.ny * G.nz;
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -658,7 +776,7 @@ __global__ void k_macro(Store st, Geom G, Phys P, int layout, double* __restrict
   NodeMap nm;
   nm.init(G, x, y, z);
   R fr[27], fb[27];
-  load_node(st, P, nm, layout, fr, fb);
+  load_node(st, K, nm, layout, fr, fb);
   double r = 0.0, b = 0.0, j[3] = {0.0, 0.0, 0.0};
 #pragma unroll
   for (int t = 0; t < 27; ++t) {
@@ -670,14 +788,15 @@ __global__ void k_macro(Store st, Geom G, Phys P, int layout, double* __restrict
     j[2] += cz_of(t) * s;
   }
   const double rho = r + b;
-  double F[3];
-  body_force(P, rho, F);
+  double k = 0.0;
+  if (K.force_mode == FORCE_BUOYANCY || K.force_mode == FORCE_DISPERSED) k = rho - (double)K.rho_ref;
+  else if (K.force_mode == FORCE_UNIFORM) k = 1.0;
   if (rr) rr[n] = r;
   if (rb) rb[n] = b;
   if (u) {
-    u[n] = (j[0] + 0.5 * F[0]) / rho;
-    u[N + n] = (j[1] + 0.5 * F[1]) / rho;
-    u[2 * N + n] = (j[2] + 0.5 * F[2]) / rho;
+    u[n] = (j[0] + 0.5 * k * (double)K.g[0]) / rho;
+    u[N + n] = (j[1] + 0.5 * k * (double)K.g[1]) / rho;
+    u[2 * N + n] = (j[2] + 0.5 * k * (double)K.g[2]) / rho;
   }
 }
 

@@ -33,51 +33,52 @@ struct Launch {
   using Tr = StoreTraits<Store>;
   using DT = typename DensOf<Store>::type;
   using R = typename DensOf<Store>::real;
+  static KConst<R> kc(const Phys& P) { return make_kconst<R>(P); }
 
   static cudaError_t density(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag,
                              long long* step, cudaStream_t s) {
-    k_density<Store><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(Tr::make(pop, G), G, P, layout, static_cast<DT*>(dens),
+    k_density<Store><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(Tr::make(pop, G), G, kc(P), layout, static_cast<DT*>(dens),
                                                            flag, step);
     return cudaGetLastError();
   }
   static cudaError_t collide(void* pop, const Geom& G, const Phys& P, int odd, const void* dens, const long long* step,
                              cudaStream_t s) {
-    k_collide_stream<Store, Tr::minb><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(Tr::make(pop, G), G, P, odd,
+    k_collide_stream<Store, Tr::minb><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(Tr::make(pop, G), G, kc(P), odd,
                                                                             static_cast<const DT*>(dens), step);
     return cudaGetLastError();
   }
   static cudaError_t outflow(void* pop, const Geom& G, const Phys& P, int layout, void* top, cudaStream_t s) {
     dim3 b(32, 4), g((unsigned)((G.nx + 31) / 32), (unsigned)((G.ny + 3) / 4));
-    k_outflow<Store><<<g, b, 0, s>>>(Tr::make(pop, G), G, P, layout, static_cast<R*>(top));
+    k_outflow<Store><<<g, b, 0, s>>>(Tr::make(pop, G), G, kc(P), layout, static_cast<R*>(top));
     return cudaGetLastError();
   }
   static cudaError_t init(void* pop, const Geom& G, const Phys& P, const double* rr, const double* rb, const double* u,
                           cudaStream_t s) {
     const int64_t N = (int64_t)G.nx * G.ny * G.nz;
-    k_init<Store><<<blocks1(N, 256), 256, 0, s>>>(Tr::make(pop, G), G, P, rr, rb, u);
+    k_init<Store><<<blocks1(N, 256), 256, 0, s>>>(Tr::make(pop, G), G, kc(P), rr, rb, u);
     return cudaGetLastError();
   }
   static cudaError_t get_pop(void* pop, const Geom& G, const Phys& P, int layout, int pdir, double* out_r,
                              double* out_b, cudaStream_t s) {
     const int64_t N = (int64_t)G.nx * G.ny * G.nz;
-    k_get_pop<Store><<<blocks1(N, 256), 256, 0, s>>>(Tr::make(pop, G), G, P, layout, pdir, out_r, out_b);
+    k_get_pop<Store><<<blocks1(N, 256), 256, 0, s>>>(Tr::make(pop, G), G, kc(P), layout, pdir, out_r, out_b);
     return cudaGetLastError();
   }
   static cudaError_t set_pop(void* pop, const Geom& G, const Phys& P, int layout, int pdir, const double* in_r,
                              const double* in_b, cudaStream_t s) {
     const int64_t N = (int64_t)G.nx * G.ny * G.nz;
-    k_set_pop<Store><<<blocks1(N, 256), 256, 0, s>>>(Tr::make(pop, G), G, P, layout, pdir, in_r, in_b);
+    k_set_pop<Store><<<blocks1(N, 256), 256, 0, s>>>(Tr::make(pop, G), G, kc(P), layout, pdir, in_r, in_b);
     return cudaGetLastError();
   }
   static cudaError_t top_from_state(void* pop, const Geom& G, const Phys& P, int layout, void* top, cudaStream_t s) {
     const int64_t Pn = (int64_t)G.nx * G.ny;
-    k_top_from_state<Store><<<blocks1(Pn, 128), 128, 0, s>>>(Tr::make(pop, G), G, P, layout, static_cast<R*>(top));
+    k_top_from_state<Store><<<blocks1(Pn, 128), 128, 0, s>>>(Tr::make(pop, G), G, kc(P), layout, static_cast<R*>(top));
     return cudaGetLastError();
   }
   static cudaError_t macro(void* pop, const Geom& G, const Phys& P, int layout, double* rr, double* rb, double* u,
                            cudaStream_t s) {
     const int64_t N = (int64_t)G.nx * G.ny * G.nz;
-    k_macro<Store><<<blocks1(N, 256), 256, 0, s>>>(Tr::make(pop, G), G, P, layout, rr, rb, u);
+    k_macro<Store><<<blocks1(N, 256), 256, 0, s>>>(Tr::make(pop, G), G, kc(P), layout, rr, rb, u);
     return cudaGetLastError();
   }
   static int collide_regs() {
