@@ -240,7 +240,7 @@ def end_to_end(pkg, torch, w, rr, rb, u, args, ws, dev):
     out = (torch.empty(rr.shape, dtype=torch.float64).pin_memory(),
            torch.empty(rb.shape, dtype=torch.float64).pin_memory(),
            torch.empty(u.shape, dtype=torch.float64).pin_memory())
-    late = pkg.Lattice(shape, w["params"], storage=args.storage)
+    late = pkg.Lattice(shape, w["params"], storage=args.storage, variant=args.variant)
     late.init_fields(hr, hb, hu)
     late.step(args.warmup)
     late.synchronize()
@@ -279,6 +279,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--variant", type=int, default=0, help="collide-stream kernel: 0 library choice, 1 one node "
+                    "per thread, 2 two nodes per thread")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -306,7 +308,7 @@ def main():
     rr, rb, u = L.initial_fields(w)
 
     def make(storage):
-        lat = pkg.Lattice(shape, w["params"], storage=storage)
+        lat = pkg.Lattice(shape, w["params"], storage=storage, variant=args.variant)
         lat.init_fields(rr, rb, u)
         return lat
 

@@ -125,6 +125,10 @@ typedef struct {
                             aligned and outlive the handle.  NULL: the library
                             allocates (cudaMalloc) and frees it itself. */
   size_t workspace_bytes;
+  int variant;           /* collide-stream kernel: 0 = library's choice (currently 1),
+                            1 = one node per thread, 2 = two x-adjacent nodes per
+                            thread with packed FP32x2 arithmetic (needs F32/F16/BF16
+                            storage and an even nx) */
 } lbm_params;
 
 typedef struct lbm lbm; /* opaque handle; owns all device state it allocated */

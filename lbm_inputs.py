@@ -177,6 +177,6 @@ def parity_cases():
     rt = rayleigh_taylor(W=16, g=1e-4, Re=128.0)
     rt["params"]["A"] = 0.002
     cases.append(("rayleigh_taylor_16", rt, 0.0))
-    j = jet(nx=24, ny=20, nz=40, D=8.0, Re=200.0, nu_c=2e-3, A=0.004)
-    cases.append(("jet_24x20x40", j, 0.0))
+    j = jet(nx=32, ny=20, nz=40, D=8.0, Re=200.0, nu_c=2e-3, A=0.004)
+    cases.append(("jet_32x20x40", j, 0.0))
     return cases

@@ -44,6 +44,7 @@ struct lbm {
   int* flag;
   double *diag_out, *scratch;
   int diag_blocks;
+  int variant;  // pass-2 kernel: 1 = one node per thread, 2 = two nodes per thread
   cudaStream_t stream;
   cudaStream_t cap_stream;
   cudaGraphExec_t graph[2];  // kGraphSteps steps starting at an even / odd step
@@ -82,17 +83,6 @@ const KernelSet* kernels_for(int storage) {
   }
 }
 
-// |M_j|^2 of the moment rows as the kernels apply them (M^-1 = M^T diag(1/|M_j|^2)).
-void row_norms(double d[27]) {
-  static double M[27][27];
-  lbmk::moment_matrix_tensor(M);
-  for (int j = 0; j < 27; ++j) {
-    double s = 0.0;
-    for (int t = 0; t < 27; ++t) s += M[j][t] * M[j][t];
-    d[j] = s;
-  }
-}
-
 const char* validate(int nx, int ny, int nz, const lbm_params* p) {
   if (!p) return "params is NULL";
   if (nx < 3 || ny < 3 || nz < 3) return "each box dimension must be >= 3";
@@ -120,6 +110,9 @@ const char* validate(int nx, int ny, int nz, const lbm_params* p) {
     if (p->bc[f] == LBM_BC_OUTFLOW && f != 5) return "OUTFLOW is only allowed on the +z face";
   }
   if (p->storage < 0 || p->storage > 3) return "unknown storage";
+  if (p->variant < 0 || p->variant > 2) return "unknown kernel variant";
+  if (p->variant == 2 && (p->storage == LBM_STORE_F64 || nx % 2 != 0))
+    return "the two-nodes-per-thread kernel needs FP32 arithmetic (not F64 storage) and an even nx";
   return nullptr;
 }
 
@@ -180,7 +173,7 @@ void drop_graphs(lbm* h) {
 lbm_status enqueue_step(lbm* h, long long t, cudaStream_t s) {
   const int layout = (int)(t & 1);
   LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, h->counter, s));
-  LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, s));
+  LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->variant, s));
   if (h->p.bc[5] == LBM_BC_OUTFLOW) LBM_CUDA(h, h->ks->outflow(h->pop, h->G, h->P, (int)((t + 1) & 1), h->top, s));
   return LBM_OK;
 }
@@ -252,6 +245,9 @@ lbm_status lbm_create(int nx, int ny, int nz, const lbm_params* p, lbm** out) {
   int64_t Ns = 0;
   h->L = plan(nx, ny, nz, p, h->ks, &Ns, &h->diag_blocks);
   h->stream = static_cast<cudaStream_t>(p->cuda_stream);
+  // default: one node per thread (on GB300 it keeps 24 warps per SM resident; the
+  // two-node kernel's register footprint leaves 8 and measured slower)
+  h->variant = p->variant != 0 ? p->variant : 1;
 
   Geom& G = h->G;
   G.nx = nx;
@@ -272,12 +268,7 @@ lbm_status lbm_create(int nx, int ny, int nz, const lbm_params* p, lbm** out) {
   P.nu_b = p->nu_b;
   P.A = p->A;
   P.beta = p->beta;
-  double d[27];
-  row_norms(d);
-  for (int j = 0; j < 27; ++j) {
-    P.invd[j] = 1.0 / d[j];
-    P.kd[j] = (j < 4) ? 0.0 : p->s[j] / d[j];
-  }
+  for (int j = 0; j < 27; ++j) P.rate[j] = (j < 4 || lbmk::is_shear_moment(j)) ? 0.0 : p->s[j];
   for (int a = 0; a < 3; ++a) P.g[a] = p->g[a];
   P.force_mode = p->force_mode;
   P.rho_ref = p->force_mode == LBM_FORCE_BUOYANCY ? 0.5 * (p->rho_r0 + p->rho_b0) : p->rho_b0;
@@ -518,7 +509,7 @@ lbm_status lbm_profile_step(lbm* h, int n, double* ms_out) {
     if (cudaEventRecord(e[0], h->stream) != cudaSuccess ||
         h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, h->counter, h->stream) != cudaSuccess ||
         cudaEventRecord(e[1], h->stream) != cudaSuccess ||
-        h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->stream) != cudaSuccess ||
+        h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->variant, h->stream) != cudaSuccess ||
         cudaEventRecord(e[2], h->stream) != cudaSuccess ||
         (outflow && h->ks->outflow(h->pop, h->G, h->P, (int)((t + 1) & 1), h->top, h->stream) != cudaSuccess) ||
         cudaEventRecord(e[3], h->stream) != cudaSuccess) {

@@ -14,8 +14,9 @@ struct KernelSet {
   size_t real_bytes;      // bytes of the compute type (outflow plane history)
   cudaError_t (*density)(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag,
                          long long* step_counter, cudaStream_t s);
+  // variant: 1 = one node per thread, 2 = two nodes per thread (FP32 arithmetic, nx even)
   cudaError_t (*collide)(void* pop, const Geom& G, const Phys& P, int odd, const void* dens,
-                         const long long* step_counter, cudaStream_t s);
+                         const long long* step_counter, int variant, cudaStream_t s);
   cudaError_t (*outflow)(void* pop, const Geom& G, const Phys& P, int layout, void* top, cudaStream_t s);
   cudaError_t (*init)(void* pop, const Geom& G, const Phys& P, const double* rr, const double* rb, const double* u,
                       cudaStream_t s);
@@ -26,7 +27,7 @@ struct KernelSet {
   cudaError_t (*top_from_state)(void* pop, const Geom& G, const Phys& P, int layout, void* top, cudaStream_t s);
   cudaError_t (*macro)(void* pop, const Geom& G, const Phys& P, int layout, double* rr, double* rb, double* u,
                        cudaStream_t s);
-  int (*collide_regs)();  // registers per thread of the pass-2 kernel (from the function attributes)
+  bool has_paired;        // a two-nodes-per-thread pass 2 exists for this storage
 };
 
 const KernelSet* kernels_f64();

@@ -52,8 +52,7 @@ struct Geom {
 struct Phys {
   double rho_r0, rho_b0, alpha_r, alpha_b;
   double nu_r, nu_b, A, beta;
-  double kd[27];    // K_j / |M_j|^2 for the moments with fixed rates (0 for j < 4)
-  double invd[27];  // 1 / |M_j|^2
+  double rate[27];  // K_j for the moments with fixed rates (0 for j < 4 and the shear slots)
   double g[3];
   int force_mode;
   double rho_ref;   // reference density of the force mode
@@ -70,8 +69,7 @@ struct KConst {
   R nu_mid, nu_half;       // nu_bar = nu_mid + nu_half * phi
   R a_mid, a_half;         // alpha_bar = a_mid + a_half * phi
   R A, beta;
-  R kd[27];
-  R invd[27];
+  R rate[27];
   R g[3];
   R rho_ref;
   int force_mode;
@@ -96,10 +94,7 @@ inline KConst<R> make_kconst(const Phys& P) {
   K.a_half = (R)(0.5 * (P.alpha_r - P.alpha_b));
   K.A = (R)P.A;
   K.beta = (R)P.beta;
-  for (int j = 0; j < 27; ++j) {
-    K.kd[j] = (R)P.kd[j];
-    K.invd[j] = (R)P.invd[j];
-  }
+  for (int j = 0; j < 27; ++j) K.rate[j] = (R)P.rate[j];
   for (int a = 0; a < 3; ++a) K.g[a] = (R)P.g[a];
   K.rho_ref = (R)P.rho_ref;
   K.force_mode = P.force_mode;
@@ -133,12 +128,22 @@ __device__ __forceinline__ bool is_inlet(const Geom& g, int x, int y, int z) {
 }
 
 // fast reciprocal / inverse square root: exact in FP64 (oracle parity), MUFU in FP32
+// (the two-lane versions are in lbm_f2.cuh)
 __device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double sat_(double x) { return fmin(fmax(x, 0.0), 1.0); }
 __device__ __forceinline__ float sat_(float x) { return __saturatef(x); }
+
+// ---------------------------------------------------------------------------
+// Population storage layout: blocks of 32 consecutive storage nodes; a block
+// holds every plane (direction, colour) of its 32 nodes, 32 values per plane.
+// A warp's access to one plane is one contiguous 32-value line, and the planes
+// of a node sit at compile-time offsets from one per-node address.
+__host__ __device__ __forceinline__ int64_t elem_index(int64_t node, int planes, int plane) {
+  return ((node >> 5) * planes + plane) * 32 + (node & 31);
+}
 
 // Per-node streaming map: for each axis and side the node-index offset of the
 // neighbour, whether that side reflects the component (free-slip) and whether
@@ -191,6 +196,50 @@ struct NodeMap {
   }
 };
 
+// Streaming map of a node on a "fast row": its y and z neighbours are inside the
+// box (a warp is one x-row of a block, so this is warp-uniform), nx is a
+// multiple of 32 and neither x face bounces back.  Then a y/z shift moves whole
+// 32-node storage blocks, and S(x, t) only needs the element index of plane 0
+// of the x-shifted node, e[c_x + 1]; a specular reflection at an x face turns
+// every direction with that c_x into the one two planes away, so it is folded
+// into e as a constant plane shift.
+struct AoRow {
+  int64_t e[3];
+  template <int PLANES>
+  __device__ __forceinline__ void init(const Geom& g, int x, int y, int z) {
+    const int64_t n = snode(g, x, y, z);
+    e[1] = elem_index(n, PLANES, 0);
+    e[0] = elem_index(n - 1, PLANES, 0);
+    e[2] = elem_index(n + 1, PLANES, 0);
+    if (x == 0) e[0] = g.bc[0] == BC_PERIODIC ? elem_index(n + g.nx - 1, PLANES, 0) : e[1] + 2 * 32;
+    if (x == g.nx - 1) e[2] = g.bc[1] == BC_PERIODIC ? elem_index(n - (g.nx - 1), PLANES, 0) : e[1] - 2 * 32;
+  }
+  // element index of plane 0 of the slot S(x, t) (add the plane of t)
+  template <int T, int PLANES>
+  __device__ __forceinline__ int64_t slot0(const Geom& g) const {
+    return e[cx_of(T) + 1] + (int64_t)((cy_of(T) * g.nx + cz_of(T) * (g.nx * g.ny)) >> 5) * (PLANES * 32);
+  }
+};
+
+__device__ __forceinline__ bool fast_row(const Geom& g, int y, int z) {
+  return y > 0 && y < g.ny - 1 && z > 0 && z < g.nz - 1 && (g.nx & 31) == 0 && g.bc[0] != BC_NOSLIP &&
+         g.bc[1] != BC_NOSLIP;
+}
+
+__device__ __forceinline__ bool yz_interior(const Geom& g, int y, int z) {
+  return y > 0 && y < g.ny - 1 && z > 0 && z < g.nz - 1;
+}
+
+// node-index offset of c_t (interior nodes: S(x, t) = (x + c_t, t)); strides from the
+// kernel parameters, so the offsets are warp-uniform
+template <int T>
+__device__ __forceinline__ int64_t interior_offset(const Geom& g) {
+  return (int64_t)(cx_of(T) + cy_of(T) * g.nx + cz_of(T) * (g.nx * g.ny));
+}
+__device__ __forceinline__ bool is_interior(const Geom& g, int x, int y, int z) {
+  return x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 && z > 0 && z < g.nz - 1;
+}
+
 // slot holding the post-streaming population (x, t) in a layout (runtime t)
 __device__ __forceinline__ void slot_of(const NodeMap& nm, int layout, int t, int64_t& node, int& dir) {
   if (layout == 0) {
@@ -217,18 +266,55 @@ __device__ __forceinline__ void slot_of(const NodeMap& nm, int layout, int t, in
 template <typename T>
 struct PlainStore {  // FP64 or FP32: f^r and f^b planes [2][27][Ns]
   using real = T;
+  static constexpr int PLANES = 54;  // (colour, direction): red 0..26, blue 27..53
   T* A;
   int64_t Ns;
+  // loads return the red population and the total f = f^r + f^b
   template <typename R>
-  __device__ __forceinline__ void load(int64_t node, int dir, int, const KConst<R>&, R& fr, R& fb) const {
-    fr = (R)__ldcs(A + (int64_t)dir * Ns + node);
-    fb = (R)__ldcs(A + (int64_t)(27 + dir) * Ns + node);
+  __device__ __forceinline__ void load(int64_t node, int dir, int, const KConst<R>&, R& fr, R& ft) const {
+    fr = (R)__ldcs(A + elem_index(node, PLANES, dir));
+    ft = fr + (R)__ldcs(A + elem_index(node, PLANES, 27 + dir));
+  }
+  // accessors by the element index e0 of plane 0 of a node (fast rows)
+  template <typename R>
+  __device__ __forceinline__ void load_at(int64_t e0, int dir, int, const KConst<R>&, R& fr, R& ft) const {
+    fr = (R)__ldcs(A + e0 + dir * 32);
+    ft = fr + (R)__ldcs(A + e0 + (27 + dir) * 32);
+  }
+  template <typename R>
+  __device__ __forceinline__ void store_at(int64_t e0, int dir, int, const KConst<R>&, R outr, R outb, R, R) const {
+    __stcs(A + e0 + dir * 32, (T)outr);
+    __stcs(A + e0 + (27 + dir) * 32, (T)outb);
+  }
+  // the two colours as stored (I/O kernels)
+  template <typename R>
+  __device__ __forceinline__ void load_rb(int64_t node, int dir, int, const KConst<R>&, R& fr, R& fb) const {
+    fr = (R)A[elem_index(node, PLANES, dir)];
+    fb = (R)A[elem_index(node, PLANES, 27 + dir)];
   }
   // outr, outb: the two colours; fstar = outr + outb and q = outr / fstar are for packed storage
   template <typename R>
   __device__ __forceinline__ void store(int64_t node, int dir, int, const KConst<R>&, R outr, R outb, R, R) const {
-    __stcs(A + (int64_t)dir * Ns + node, (T)outr);
-    __stcs(A + (int64_t)(27 + dir) * Ns + node, (T)outb);
+    __stcs(A + elem_index(node, PLANES, dir), (T)outr);
+    __stcs(A + elem_index(node, PLANES, 27 + dir), (T)outb);
+  }
+  // two-node accessors (FP32 only): nodes `node` (even) and node+1 of one plane row
+  __device__ __forceinline__ void load_s(int64_t node, int dir, float, float, float& fr, float& ft) const {
+    fr = (float)__ldcs(A + elem_index(node, PLANES, dir));
+    ft = fr + (float)__ldcs(A + elem_index(node, PLANES, 27 + dir));
+  }
+  __device__ __forceinline__ void store_s(int64_t node, int dir, float, float, float outr, float outb, float,
+                                          float) const {
+    __stcs(A + elem_index(node, PLANES, dir), (T)outr);
+    __stcs(A + elem_index(node, PLANES, 27 + dir), (T)outb);
+  }
+  __device__ __forceinline__ void load_p(int64_t node, int dir, float, float, F2& fr, F2& ft) const {
+    fr = F2(__ldcs(reinterpret_cast<const float2*>(A + elem_index(node, PLANES, dir))));
+    ft = fr + F2(__ldcs(reinterpret_cast<const float2*>(A + elem_index(node, PLANES, 27 + dir))));
+  }
+  __device__ __forceinline__ void store_p(int64_t node, int dir, float, float, F2 outr, F2 outb, F2, F2) const {
+    __stcs(reinterpret_cast<float2*>(A + elem_index(node, PLANES, dir)), outr.v);
+    __stcs(reinterpret_cast<float2*>(A + elem_index(node, PLANES, 27 + dir)), outb.v);
   }
 };
 
@@ -242,6 +328,7 @@ struct PlainStore {  // FP64 or FP32: f^r and f^b planes [2][27][Ns]
 template <bool BF16>
 struct PackedStore {
   using real = float;
+  static constexpr int PLANES = 27;
   uint32_t* A;
   int64_t Ns;
   __device__ __forceinline__ static float dev_to_float(uint32_t bits) {
@@ -256,23 +343,66 @@ struct PackedStore {
   __device__ __forceinline__ static float code_to_float(uint32_t k) {
     return __uint_as_float(0x4B000000u | k) - 8388608.0f;
   }
-  template <typename R>
-  __device__ __forceinline__ void load(int64_t node, int dir, int cls, const KConst<R>& K, R& fr, R& fb) const {
-    const uint32_t w = __ldcs(A + (int64_t)dir * Ns + node);
+  // word -> (f^r, f); rB, dR: rest-state value of the direction's speed class
+  __device__ __forceinline__ static void decode(uint32_t w, float rB, float dR, float& fr, float& f) {
     const float q = code_to_float(w >> 16) * (1.0f / 65535.0f);
-    const float f = fmaf(q, (float)K.dref[cls], (float)K.refB[cls]) + dev_to_float(w);
-    const float r = q * f;
-    fr = (R)r;
-    fb = (R)(f - r);
+    f = fmaf(q, dR, rB) + dev_to_float(w);
+    fr = q * f;
+  }
+  // (f*, q) -> word
+  __device__ __forceinline__ static uint32_t encode(float rB, float dR, float fstar, float q) {
+    const float qk = fmaf(__saturatef(q), 65535.0f, 8388608.0f);  // rounds to the nearest code
+    const uint32_t k = __float_as_uint(qk) & 0xFFFFu;
+    const float qq = (qk - 8388608.0f) * (1.0f / 65535.0f);
+    return (k << 16) | float_to_dev(fstar - fmaf(qq, dR, rB));
+  }
+  template <typename R>
+  __device__ __forceinline__ void load(int64_t node, int dir, int cls, const KConst<R>& K, R& fr, R& ft) const {
+    float a, b;
+    decode(__ldcs(A + elem_index(node, PLANES, dir)), (float)K.refB[cls], cls == 0 ? (float)K.dref[0] : 0.0f, a, b);
+    fr = (R)a;
+    ft = (R)b;
+  }
+  template <typename R>
+  __device__ __forceinline__ void load_at(int64_t e0, int dir, int cls, const KConst<R>& K, R& fr, R& ft) const {
+    float a, b;
+    decode(__ldcs(A + e0 + dir * 32), (float)K.refB[cls], cls == 0 ? (float)K.dref[0] : 0.0f, a, b);
+    fr = (R)a;
+    ft = (R)b;
+  }
+  template <typename R>
+  __device__ __forceinline__ void store_at(int64_t e0, int dir, int cls, const KConst<R>& K, R, R, R fstar,
+                                           R q) const {
+    __stcs(A + e0 + dir * 32, encode((float)K.refB[cls], cls == 0 ? (float)K.dref[0] : 0.0f, (float)fstar, (float)q));
+  }
+  template <typename R>
+  __device__ __forceinline__ void load_rb(int64_t node, int dir, int cls, const KConst<R>& K, R& fr, R& fb) const {
+    R ft;
+    load(node, dir, cls, K, fr, ft);
+    fb = ft - fr;
   }
   template <typename R>
   __device__ __forceinline__ void store(int64_t node, int dir, int cls, const KConst<R>& K, R, R, R fstar,
                                         R q) const {
-    const float qk = fmaf(__saturatef((float)q), 65535.0f, 8388608.0f);  // rounds to the nearest code
-    const uint32_t k = __float_as_uint(qk) & 0xFFFFu;
-    const float qq = (qk - 8388608.0f) * (1.0f / 65535.0f);
-    const float ref = fmaf(qq, (float)K.dref[cls], (float)K.refB[cls]);
-    __stcs(A + (int64_t)dir * Ns + node, (k << 16) | float_to_dev((float)fstar - ref));
+    __stcs(A + elem_index(node, PLANES, dir),
+           encode((float)K.refB[cls], cls == 0 ? (float)K.dref[0] : 0.0f, (float)fstar, (float)q));
+  }
+  // two-node accessors: nodes `node` (even) and node+1 of one plane row
+  __device__ __forceinline__ void load_s(int64_t node, int dir, float rB, float dR, float& fr, float& ft) const {
+    decode(__ldcs(A + elem_index(node, PLANES, dir)), rB, dR, fr, ft);
+  }
+  __device__ __forceinline__ void store_s(int64_t node, int dir, float rB, float dR, float, float, float fstar,
+                                          float q) const {
+    __stcs(A + elem_index(node, PLANES, dir), encode(rB, dR, fstar, q));
+  }
+  __device__ __forceinline__ void load_p(int64_t node, int dir, float rB, float dR, F2& fr, F2& ft) const {
+    const uint2 w = __ldcs(reinterpret_cast<const uint2*>(A + elem_index(node, PLANES, dir)));
+    decode(w.x, rB, dR, fr.v.x, ft.v.x);
+    decode(w.y, rB, dR, fr.v.y, ft.v.y);
+  }
+  __device__ __forceinline__ void store_p(int64_t node, int dir, float rB, float dR, F2, F2, F2 fstar, F2 q) const {
+    __stcs(reinterpret_cast<uint2*>(A + elem_index(node, PLANES, dir)),
+           make_uint2(encode(rB, dR, fstar.v.x, q.v.x), encode(rB, dR, fstar.v.y, q.v.y)));
   }
 };
 
@@ -282,20 +412,46 @@ template <>
 struct DensOf<PlainStore<double>> { using type = double2; using real = double; };
 
 // ---------------------------------------------------------------------------
-// load all 27 x 2 populations of a node with the layout of the step about to run
+// load all 27 directions of a node (red and total population) with the layout of the step about to run
 template <class Store, typename R>
 __device__ __forceinline__ void load_node(const Store& st, const KConst<R>& K, const NodeMap& nm, int layout,
-                                          R fr[27], R fb[27]) {
+                                          R fr[27], R ft[27]) {
   if (layout == 0) {
 #pragma unroll
-    for (int t = 0; t < 27; ++t) st.load(nm.base, t, speed2_of(t), K, fr[t], fb[t]);
+    for (int t = 0; t < 27; ++t) st.load(nm.base, t, speed2_of(t), K, fr[t], ft[t]);
   } else {
 #pragma unroll
     for (int t = 0; t < 27; ++t) {
       int64_t node;
       int dir;
       slot_of(nm, 1, t, node, dir);
-      st.load(node, dir, speed2_of(t), K, fr[t], fb[t]);
+      st.load(node, dir, speed2_of(t), K, fr[t], ft[t]);
+    }
+  }
+}
+
+// loads of a node on a fast row: even steps read plane t of the node itself,
+// odd steps the slot S(x, opp(t))
+template <class Store, typename R>
+__device__ __forceinline__ void load_node_fast(const Store& st, const KConst<R>& K, const Geom& G, const AoRow& ar,
+                                               int odd, R fr[27], R ft[27]) {
+  if (!odd) {
+#pragma unroll
+    for (int t = 0; t < 27; ++t) st.load_at(ar.e[1], t, speed2_of(t), K, fr[t], ft[t]);
+  } else {
+#pragma unroll
+    for (int t = 0; t < 27; ++t) {
+      int64_t e0;
+      switch (26 - t) {
+#define LBMK_CASE(k) case k: e0 = ar.slot0<k, Store::PLANES>(G); break;
+        LBMK_CASE(0) LBMK_CASE(1) LBMK_CASE(2) LBMK_CASE(3) LBMK_CASE(4) LBMK_CASE(5) LBMK_CASE(6)
+        LBMK_CASE(7) LBMK_CASE(8) LBMK_CASE(9) LBMK_CASE(10) LBMK_CASE(11) LBMK_CASE(12) LBMK_CASE(13)
+        LBMK_CASE(14) LBMK_CASE(15) LBMK_CASE(16) LBMK_CASE(17) LBMK_CASE(18) LBMK_CASE(19) LBMK_CASE(20)
+        LBMK_CASE(21) LBMK_CASE(22) LBMK_CASE(23) LBMK_CASE(24) LBMK_CASE(25)
+        default: e0 = ar.slot0<26, Store::PLANES>(G); break;
+#undef LBMK_CASE
+      }
+      st.load_at(e0, opp_of(t), speed2_of(t), K, fr[t], ft[t]);
     }
   }
 }
@@ -317,49 +473,50 @@ struct Recol {
   R frac;        // rho_r / rho
   R n0, n1, n2;  // unit normal grad(phi)/|grad(phi)| (0 where undefined)
   R rc[4];       // beta rho_r rho_b / rho * varphi_i(alpha_bar) / |c_i| per speed class (rc[0] unused)
-  bool has_n;
+  typename MaskOf<R>::type has_n;
 };
 
-// Collision of one node.  fr/fb: post-streaming populations (in).  On return
+// Collision of one node.  fr/ft: post-streaming red and total populations (in).  On return
 // f[t] holds f*_t, the total post-collision population including forcing and
 // perturbation, and the returned Recol splits it into colours:
 //   f^r_t = frac f*_t + rc[|c_t|^2] (c_t . n),   f^b_t = f*_t - f^r_t.
 //
 // The operators are linear in the colours, so the MRT step acts on the total f
-// (R4).  With the total equilibrium of Eq. (EES) summed over k and the
-// forcing of Eq. (ketFd),
-//   h_i = f_i - f^(e)_i + F'_i/2 = f_i - w_i Q(c_i) - delta_{i,rest} E,
-//   Q(c) = C0 + c.V + c.S.c,   C0 = P - 3/2 rho u^2 + 3/2 u.F,   V = 3 rho u - 3/2 F,
-//   S = 9/2 rho u u + 9/2 nu_bar (u g + g u) - 9/4 (u F + F u),
-//   E = sum_k rho_k alpha_k - w_rest P - 3 nu_bar u.g,   P = sum_k rho_k crest_k,
-// (g = grad rho; Phi_i = 9 w_i nu_bar (c.u)(c.g) for moving i, Eq. Phi with
-// 16/4/1 / 48 * 2 = 9 w_i).  The raw moments of w_i c^p are products of the
-// D1Q3 weight moments (1, 0, 1/3), so the raw moments of h are those of f
-// (one cascade) minus closed forms.  Then f* = f + M^-1(-K M h) + F' + Omega^(2)
-// with M^-1 = M^T diag(1/|M_j|^2) (Eq. scoll, Eq. ketF), and
-// Omega^(2)_i = A |grad phi| [w_i (c.n)^2 - B_i], B_i = w_i for moving i and
-// -10/27 at rest (Eq. perturb with the square, R1; Eq. B_i).
+// (R4), and it is carried out on the raw moments R_abc = sum_i cx^a cy^b cz^c f_i:
+//   f* = f + M^-1 (-K M h) + F' + Omega^(2),   h = f - f^(e) + F'/2
+// (Eq. scoll with Eqs. ketF-ketFd), M = T V3 (V3: raw moments, T: the sparse map
+// of Eq. momentSet).  Every term but f has the form w_i Q(c_i) + delta_{i,rest} E
+// with Q quadratic in c:
+//   f^(e) - F'/2:  C0 = P - 3/2 rho u^2 + 3/2 u.F,  V = 3 rho u - 3/2 F,
+//                  S = 9/2 rho u u + 9/2 nu_bar (u g + g u) - 9/4 (u F + F u)
+//                  (Eq. EES summed over k, Eq. varphi_ik, Eq. Phi: 16/4/1 / 48 * 2 = 9 w_i),
+//   F' + Omega^(2): C0 = -3 u.F - A|grad phi|,  V = 3 F,
+//                  S = 9/2 (u F + F u) + A|grad phi| n n
+//                  (Eq. ketFd; Eq. perturb with the square, R1, and B_i = w_i for
+//                  moving i, -10/27 at rest, Eq. B_i),
+// (P = sum_k rho_k crest_k, g = grad rho, n = grad phi/|grad phi|), whose raw
+// moments are closed forms; the rest-direction terms only touch R000 (mass),
+// which no step changes.  So: R(f) by one cascade, m = T (R(f) - closed) for
+// moments 5..27 (mass and momentum of h vanish), R* = R(f) + T^-1(-K m) +
+// closed(F' + Omega^(2)), and f* = V3^-1 R* by one inverse cascade.
 template <typename R>
-__device__ __forceinline__ Recol<R> collide(const KConst<R>& K, const R fr[27], const R fb[27], const R gphi[3],
+__device__ __forceinline__ Recol<R> collide(const KConst<R>& K, const R fr[27], const R ft[27], const R gphi[3],
                                             const R grho[3], R f[27]) {
   R rho_r = R(0);
 #pragma unroll
-  for (int t = 0; t < 27; ++t) rho_r += fr[t];
-  R r[27];
-#pragma unroll
   for (int t = 0; t < 27; ++t) {
-    f[t] = fr[t] + fb[t];
-    r[t] = f[t];
+    rho_r += fr[t];
+    f[t] = ft[t];
   }
-  raw_forward(r);
-  const R rho = r[0];
+  raw_forward(f);  // f holds R(f) from here until raw_inverse
+  const R rho = f[0];
   const R rho_b = rho - rho_r;
   const R inv_rho = rcp_(rho);
   R F[3];
   body_force(K, rho, F);
-  const R u0 = (r[1] + R(0.5) * F[0]) * inv_rho;
-  const R u1 = (r[3] + R(0.5) * F[1]) * inv_rho;
-  const R u2 = (r[9] + R(0.5) * F[2]) * inv_rho;
+  const R u0 = (f[1] + R(0.5) * F[0]) * inv_rho;
+  const R u1 = (f[3] + R(0.5) * F[1]) * inv_rho;
+  const R u2 = (f[9] + R(0.5) * F[2]) * inv_rho;
   const R phi = (rho_r - rho_b) * inv_rho;
   const R nubar = K.nu_mid + K.nu_half * phi;
   const R s_sh = rcp_(R(3) * nubar + R(0.5));
@@ -368,71 +525,54 @@ __device__ __forceinline__ Recol<R> collide(const KConst<R>& K, const R fr[27], 
   const R uu = u0 * u0 + u1 * u1 + u2 * u2;
   const R uF = u0 * F[0] + u1 * F[1] + u2 * F[2];
 
-  // closed-form raw moments of w_i Q(c_i), subtracted from those of f
-  // (delta_rest E only enters R000, which is set to its exact value 0)
-  const R C0 = Pr - R(1.5) * rho * uu + R(1.5) * uF;
-  const R V0 = R(3) * rho * u0 - R(1.5) * F[0];
-  const R V1 = R(3) * rho * u1 - R(1.5) * F[1];
-  const R V2 = R(3) * rho * u2 - R(1.5) * F[2];
-  const R r45 = R(4.5) * rho, n45 = R(4.5) * nubar;
-  const R Sxx = r45 * u0 * u0 + R(2) * n45 * u0 * g0 - R(4.5) * u0 * F[0];
-  const R Syy = r45 * u1 * u1 + R(2) * n45 * u1 * g1 - R(4.5) * u1 * F[1];
-  const R Szz = r45 * u2 * u2 + R(2) * n45 * u2 * g2 - R(4.5) * u2 * F[2];
-  const R Sxy = r45 * u0 * u1 + n45 * (u0 * g1 + u1 * g0) - R(2.25) * (u0 * F[1] + u1 * F[0]);
-  const R Syz = r45 * u1 * u2 + n45 * (u1 * g2 + u2 * g1) - R(2.25) * (u1 * F[2] + u2 * F[1]);
-  const R Sxz = r45 * u0 * u2 + n45 * (u0 * g2 + u2 * g0) - R(2.25) * (u0 * F[2] + u2 * F[0]);
-  const R t3 = R(1.0 / 3.0), t9 = R(1.0 / 9.0), t27 = R(1.0 / 27.0);
-#define LBMK_IX(a, b, c) ((a) + 3 * (b) + 9 * (c))
-  // mass and momentum of h vanish identically (conserved by the equilibrium with the F/2 shift)
-  r[LBMK_IX(0, 0, 0)] = R(0);
-  r[LBMK_IX(1, 0, 0)] = R(0);
-  r[LBMK_IX(0, 1, 0)] = R(0);
-  r[LBMK_IX(0, 0, 1)] = R(0);
-  r[LBMK_IX(2, 0, 0)] -= t3 * (C0 + Sxx) + t9 * (Syy + Szz);
-  r[LBMK_IX(0, 2, 0)] -= t3 * (C0 + Syy) + t9 * (Sxx + Szz);
-  r[LBMK_IX(0, 0, 2)] -= t3 * (C0 + Szz) + t9 * (Sxx + Syy);
-  r[LBMK_IX(2, 2, 0)] -= t9 * (C0 + Sxx + Syy) + t27 * Szz;
-  r[LBMK_IX(2, 0, 2)] -= t9 * (C0 + Sxx + Szz) + t27 * Syy;
-  r[LBMK_IX(0, 2, 2)] -= t9 * (C0 + Syy + Szz) + t27 * Sxx;
-  r[LBMK_IX(2, 2, 2)] -= t27 * (C0 + Sxx + Syy + Szz);
-  r[LBMK_IX(1, 2, 0)] -= t9 * V0;
-  r[LBMK_IX(1, 0, 2)] -= t9 * V0;
-  r[LBMK_IX(1, 2, 2)] -= t27 * V0;
-  r[LBMK_IX(2, 1, 0)] -= t9 * V1;
-  r[LBMK_IX(0, 1, 2)] -= t9 * V1;
-  r[LBMK_IX(2, 1, 2)] -= t27 * V1;
-  r[LBMK_IX(2, 0, 1)] -= t9 * V2;
-  r[LBMK_IX(0, 2, 1)] -= t9 * V2;
-  r[LBMK_IX(2, 2, 1)] -= t27 * V2;
-  r[LBMK_IX(1, 1, 0)] -= R(2) * t9 * Sxy;
-  r[LBMK_IX(1, 1, 2)] -= R(2) * t27 * Sxy;
-  r[LBMK_IX(0, 1, 1)] -= R(2) * t9 * Syz;
-  r[LBMK_IX(2, 1, 1)] -= R(2) * t27 * Syz;
-  r[LBMK_IX(1, 0, 1)] -= R(2) * t9 * Sxz;
-  r[LBMK_IX(1, 2, 1)] -= R(2) * t27 * Sxz;
-  // R111 of w Q is zero
-#undef LBMK_IX
-
+  // raw moments of h (mass and momentum of h vanish identically)
+  R h[27];
+#pragma unroll
+  for (int t = 0; t < 27; ++t) h[t] = f[t];
+  {
+    const R C0 = Pr - R(1.5) * rho * uu + R(1.5) * uF;
+    const R V[3] = {R(3) * rho * u0 - R(1.5) * F[0], R(3) * rho * u1 - R(1.5) * F[1], R(3) * rho * u2 - R(1.5) * F[2]};
+    const R r45 = R(4.5) * rho, n45 = R(4.5) * nubar;
+    const R S[6] = {r45 * u0 * u0 + R(2) * n45 * u0 * g0 - R(4.5) * u0 * F[0],
+                    r45 * u1 * u1 + R(2) * n45 * u1 * g1 - R(4.5) * u1 * F[1],
+                    r45 * u2 * u2 + R(2) * n45 * u2 * g2 - R(4.5) * u2 * F[2],
+                    r45 * u0 * u1 + n45 * (u0 * g1 + u1 * g0) - R(2.25) * (u0 * F[1] + u1 * F[0]),
+                    r45 * u1 * u2 + n45 * (u1 * g2 + u2 * g1) - R(2.25) * (u1 * F[2] + u2 * F[1]),
+                    r45 * u0 * u2 + n45 * (u0 * g2 + u2 * g0) - R(2.25) * (u0 * F[2] + u2 * F[0])};
+    closed_raw_add(h, R(-1), C0, V, S);
+  }
+  h[0] = R(0);
+  h[1] = R(0);
+  h[3] = R(0);
+  h[9] = R(0);
   R m[27];
-  moment_forward(r, m);
-  R y[27];
+  moment_forward(h, m);
 #pragma unroll
-  for (int j = 0; j < 4; ++j) y[j] = R(0);
+  for (int j = 0; j < 4; ++j) m[j] = R(0);
 #pragma unroll
-  for (int j = 4; j < 27; ++j) y[j] = -(is_shear_moment(j) ? s_sh * K.invd[j] : K.kd[j]) * m[j];
-  moment_adjoint(y, r);
-  raw_adjoint(r);
+  for (int j = 4; j < 27; ++j) m[j] = -(is_shear_moment(j) ? s_sh : K.rate[j]) * m[j];  // -K (M h)
+  moment_inverse_add(m, f);
 
   // perturbation and recolouring scalars
   Recol<R> out;
   const R G0 = gphi[0], G1 = gphi[1], G2 = gphi[2];
   const R gg = G0 * G0 + G1 * G1 + G2 * G2;
-  out.has_n = gg > R(1e-24);
-  const R inv_gn = out.has_n ? rsqrt_(gg) : R(0);
+  out.has_n = gt_(gg, R(1e-24));
+  const R inv_gn = select_(out.has_n, rsqrt_(gg), R(0));
   out.n0 = G0 * inv_gn;
   out.n1 = G1 * inv_gn;
   out.n2 = G2 * inv_gn;
   const R Ag = K.A * gg * inv_gn;  // A |grad phi|
+  {
+    const R V[3] = {R(3) * F[0], R(3) * F[1], R(3) * F[2]};
+    const R S[6] = {R(9) * u0 * F[0] + Ag * out.n0 * out.n0, R(9) * u1 * F[1] + Ag * out.n1 * out.n1,
+                    R(9) * u2 * F[2] + Ag * out.n2 * out.n2, R(4.5) * (u0 * F[1] + u1 * F[0]) + Ag * out.n0 * out.n1,
+                    R(4.5) * (u1 * F[2] + u2 * F[1]) + Ag * out.n1 * out.n2,
+                    R(4.5) * (u0 * F[2] + u2 * F[0]) + Ag * out.n0 * out.n2};
+    closed_raw_add(f, R(1), R(-3) * uF - Ag, V, S);
+  }
+  raw_inverse(f);  // f holds f*
+
   const R abar = K.a_mid + K.a_half * phi;
   const R cr = K.beta * rho_r * rho_b * inv_rho * R(27.0 / 19.0) * (R(1) - abar);
   out.frac = rho_r * inv_rho;
@@ -440,25 +580,6 @@ __device__ __forceinline__ Recol<R> collide(const KConst<R>& K, const R fr[27], 
   out.rc[1] = cr * R(weight_of(tensor_index(1, 0, 0)));
   out.rc[2] = cr * R(weight_of(tensor_index(1, 1, 0)) * 0.70710678118654752440);
   out.rc[3] = cr * R(weight_of(tensor_index(1, 1, 1)) * 0.57735026918962576451);
-  const R Aw1 = Ag * R(weight_of(tensor_index(1, 0, 0)));
-  const R Aw2 = Ag * R(weight_of(tensor_index(1, 1, 0)));
-  const R Aw3 = Ag * R(weight_of(tensor_index(1, 1, 1)));
-  const R uF3 = R(3) * uF;
-
-#pragma unroll
-  for (int t = 0; t < 27; ++t) {
-    if (t == REST) {
-      f[t] = f[t] + r[t] - R(weight_of(REST)) * uF3 + Ag * R(10.0 / 27.0);
-    } else {
-      const R w = R(weight_of(t));
-      const R cu = R(cx_of(t)) * u0 + R(cy_of(t)) * u1 + R(cz_of(t)) * u2;
-      const R cF = R(cx_of(t)) * F[0] + R(cy_of(t)) * F[1] + R(cz_of(t)) * F[2];
-      const R cn = R(cx_of(t)) * out.n0 + R(cy_of(t)) * out.n1 + R(cz_of(t)) * out.n2;
-      const R Aw = speed2_of(t) == 1 ? Aw1 : (speed2_of(t) == 2 ? Aw2 : Aw3);
-      const R fp = (R(9) * w * cu) * cF + w * (R(3) * cF - uF3);  // F'_t (Eq. ketFd)
-      f[t] = f[t] + r[t] + fp + (Aw * cn * cn - Aw);
-    }
-  }
   return out;
 }
 
@@ -476,7 +597,7 @@ __device__ __forceinline__ void inlet_state(const KConst<R>& K, int64_t node_lin
 #pragma unroll
   for (int t = 0; t < 27; ++t) {
     const R w = (R)weight_of(t);
-    const R cu = R(cx_of(t)) * u0 + R(cy_of(t)) * u1 + R(cz_of(t)) * u2;
+    const R cu = R(cx_of(t)) * u0 + R(cy_of(t)) * u1 + R(cz_of(t)) * u2;  // inlet nodes only
     const R vphi = t == REST ? ar : R(27.0 / 19.0) * (R(1) - ar) * w;
     f[t] = rho * (vphi + w * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));
   }
@@ -488,23 +609,27 @@ __device__ __forceinline__ int wrap_or_clamp(int q, int n, int bc_lo, int bc_hi)
   return q;
 }
 
-// write direction T of the node (step parity `odd`): colours, f* and red fraction
-template <int T, class Store, typename R>
-__device__ __forceinline__ void emit(const Store& st, const KConst<R>& K, const NodeMap& nm, bool odd, const R f[27],
-                                     const Recol<R>& rc) {
+// write direction T of the node (step parity `odd`): colours, f* and red fraction.
+// RECOL: some node of the warp has an interface normal (otherwise the
+// recolouring term is zero and the red fraction of every direction is rho_r/rho).
+template <int T, bool FAST, bool RECOL, class Store, typename R>
+__device__ __forceinline__ void emit(const Store& st, const KConst<R>& K, const Geom& G, const NodeMap& nm,
+                                     const AoRow& ar, bool odd, const R f[27], const Recol<R>& rc) {
   const R fstar = f[T];
   R outr, q;
-  if (T == REST) {
+  if (T == REST || !RECOL) {
     outr = rc.frac * fstar;
     q = rc.frac;
   } else {
-    const R cn = R(cx_of(T)) * rc.n0 + R(cy_of(T)) * rc.n1 + R(cz_of(T)) * rc.n2;
-    const R rcol = rc.rc[speed2_of(T)] * cn;
-    outr = rc.frac * fstar + rcol;
-    q = rc.has_n ? sat_(outr * rcp_(fstar)) : rc.frac;
+    const R cn = cdot<T>(rc.n0, rc.n1, rc.n2);
+    outr = fma_(rc.rc[speed2_of(T)], cn, rc.frac * fstar);
+    q = sat_(outr * rcp_(fstar));
   }
   const R outb = fstar - outr;
-  if (!odd) {
+  if (FAST) {
+    if (!odd) st.store_at(ar.e[1], opp_of(T), speed2_of(T), K, outr, outb, fstar, q);
+    else st.store_at(ar.slot0<T, Store::PLANES>(G), T, speed2_of(T), K, outr, outb, fstar, q);
+  } else if (!odd) {
     st.store(nm.base, opp_of(T), speed2_of(T), K, outr, outb, fstar, q);
   } else {
     int64_t node;
@@ -514,18 +639,18 @@ __device__ __forceinline__ void emit(const Store& st, const KConst<R>& K, const 
   }
 }
 
-template <int T, class Store, typename R>
+template <int T, class Store, typename R, bool FAST, bool RECOL>
 struct EmitLoop {
-  __device__ __forceinline__ static void run(const Store& st, const KConst<R>& K, const NodeMap& nm, bool odd,
-                                             const R* f, const Recol<R>& rc) {
-    emit<T>(st, K, nm, odd, f, rc);
-    EmitLoop<T + 1, Store, R>::run(st, K, nm, odd, f, rc);
+  __device__ __forceinline__ static void run(const Store& st, const KConst<R>& K, const Geom& G, const NodeMap& nm,
+                                             const AoRow& ar, bool odd, const R* f, const Recol<R>& rc) {
+    emit<T, FAST, RECOL>(st, K, G, nm, ar, odd, f, rc);
+    EmitLoop<T + 1, Store, R, FAST, RECOL>::run(st, K, G, nm, ar, odd, f, rc);
   }
 };
-template <class Store, typename R>
-struct EmitLoop<27, Store, R> {
-  __device__ __forceinline__ static void run(const Store&, const KConst<R>&, const NodeMap&, bool, const R*,
-                                             const Recol<R>&) {}
+template <class Store, typename R, bool FAST, bool RECOL>
+struct EmitLoop<27, Store, R, FAST, RECOL> {
+  __device__ __forceinline__ static void run(const Store&, const KConst<R>&, const Geom&, const NodeMap&,
+                                             const AoRow&, bool, const R*, const Recol<R>&) {}
 };
 
 // ---------------------------------------------------------------------------
@@ -544,16 +669,23 @@ __global__ void __launch_bounds__(NTHREADS) k_density(Store st, Geom G,
   const int y = blockIdx.y * BY + threadIdx.y;
   const int z = blockIdx.z * BZ + threadIdx.z;
   if (x >= G.nx || y >= G.ny || z >= G.nz) return;
-  NodeMap nm;
-  nm.init(G, x, y, z);
-  D fr[27], fb[27];
-  load_node(st, K, nm, layout, fr, fb);
-  D rr = D(0), rb = D(0);
+  D fr[27], ft[27];
+  if (fast_row(G, y, z)) {
+    AoRow ar;
+    ar.init<Store::PLANES>(G, x, y, z);
+    load_node_fast(st, K, G, ar, layout, fr, ft);
+  } else {
+    NodeMap nm;
+    nm.init(G, x, y, z);
+    load_node(st, K, nm, layout, fr, ft);
+  }
+  D rr = D(0), rt = D(0);
 #pragma unroll
   for (int t = 0; t < 27; ++t) {
     rr += fr[t];
-    rb += fb[t];
+    rt += ft[t];
   }
+  D rb = rt - rr;
   if (is_inlet(G, x, y, z)) {
     rr = (D)K.rho_r0_d;
     rb = D(0);
@@ -580,22 +712,43 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
   const bool active = x < G.nx && y < G.ny && z < G.nz;
 
-  NodeMap nm;
-  R fr[27], fb[27];
+  R fr[27], ft[27];
+  // a warp is one x-row of the block: the fast-row test is warp-uniform
+  const bool fast = fast_row(G, y, z);
+  const int64_t base = snode(G, x, y, z);
+  AoRow ar;
+  if (fast) ar.init<Store::PLANES>(G, x, y, z);
   if (active) {
-    nm.init(G, x, y, z);
-    load_node(st, K, nm, odd, fr, fb);
+    if (fast) {
+      load_node_fast(st, K, G, ar, odd, fr, ft);
+    } else {
+      NodeMap nm;
+      nm.init(G, x, y, z);
+      load_node(st, K, nm, odd, fr, ft);
+    }
   }
 
-  const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
-  for (int e = tid; e < TILE; e += NTHREADS) {
-    const int tx = e % TX, ty = (e / TX) % TY, tz = e / (TX * TY);
-    const int gx = wrap_or_clamp(x0 + tx - 1, G.nx, G.bc[0], G.bc[1]);
-    const int gy = wrap_or_clamp(y0 + ty - 1, G.ny, G.bc[2], G.bc[3]);
-    const int gz = wrap_or_clamp(z0 + tz - 1, G.nz, G.bc[4], G.bc[5]);
-    // out-of-box tail threads of a ragged block read a clamped in-box node
-    const int cx = gx < G.nx ? gx : G.nx - 1, cy = gy < G.ny ? gy : G.ny - 1, cz = gz < G.nz ? gz : G.nz - 1;
-    tile[e] = dens[dnode(G, cx, cy, cz)];
+  // halo tile of (rho, phi): warp w fills rows w, w+8, w+16 of the TY*TZ rows of TX
+  // values; lanes cover x0-1 .. x0+30 and lanes 0..1 also x0+31, x0+32.
+  {
+    const int warp = (threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z)) >> 5, lane = threadIdx.x;
+    const int xa = wrap_or_clamp(x0 + lane - 1, G.nx, G.bc[0], G.bc[1]);
+    const int xb = wrap_or_clamp(x0 + lane + 31, G.nx, G.bc[0], G.bc[1]);
+    const int cxa = xa < G.nx ? xa : G.nx - 1, cxb = xb < G.nx ? xb : G.nx - 1;
+#pragma unroll
+    for (int k = 0; k < (TY * TZ + NTHREADS / 32 - 1) / (NTHREADS / 32); ++k) {
+      const int row = warp + k * (NTHREADS / 32);
+      if (row < TY * TZ) {
+        const int ty = row % TY, tz = row / TY;
+        const int gy = wrap_or_clamp(y0 + ty - 1, G.ny, G.bc[2], G.bc[3]);
+        const int gz = wrap_or_clamp(z0 + tz - 1, G.nz, G.bc[4], G.bc[5]);
+        // out-of-box tail rows of a ragged block read a clamped in-box row
+        const int64_t rbase = (int64_t)G.nx * ((int64_t)(gy < G.ny ? gy : G.ny - 1) +
+                                                (int64_t)G.ny * (gz < G.nz ? gz : G.nz - 1));
+        tile[row * TX + lane] = dens[rbase + cxa];
+        if (lane < TX - 32) tile[row * TX + 32 + lane] = dens[rbase + cxb];
+      }
+    }
   }
   __syncthreads();
   if (!active) return;
@@ -622,9 +775,174 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
     rc.rc[0] = rc.rc[1] = rc.rc[2] = rc.rc[3] = R(0);
     rc.has_n = false;
   } else {
-    rc = collide(K, fr, fb, gphi, grho, f);
+    rc = collide(K, fr, ft, gphi, grho, f);
   }
-  EmitLoop<0, Store, R>::run(st, K, nm, odd != 0, f, rc);
+  // warp-uniform: does any node of the warp carry an interface normal?
+  const bool recol = __any_sync(__activemask(), any_(rc.has_n));
+  NodeMap nm;
+  if (fast) {
+    if (recol) EmitLoop<0, Store, R, true, true>::run(st, K, G, nm, ar, odd != 0, f, rc);
+    else EmitLoop<0, Store, R, true, false>::run(st, K, G, nm, ar, odd != 0, f, rc);
+  } else {
+    if (odd) nm.init(G, x, y, z);
+    else nm.base = base;  // the even step only uses the base
+    if (recol) EmitLoop<0, Store, R, false, true>::run(st, K, G, nm, ar, odd != 0, f, rc);
+    else EmitLoop<0, Store, R, false, false>::run(st, K, G, nm, ar, odd != 0, f, rc);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pass 2, two nodes per thread (FP32 arithmetic on both lanes at once).
+// Block: 16 x 4 x 2 threads over 32 x 4 x 2 nodes; thread tx owns the node
+// pair (x0 + 2tx, x0 + 2tx + 1).  Needs nx even, so a pair is never split by
+// the box and the even node's storage index is even (8-byte aligned pairs).
+constexpr int PX = 16, PY = BY, PZ = BZ;
+constexpr int PTHREADS = PX * PY * PZ;
+
+template <int T, class Store>
+__device__ __forceinline__ void emit2(const Store& st, const KConst<F2>& K, int64_t base, const NodeMap& m0,
+                                      const NodeMap& m1, bool odd, const F2 f[27], const Recol<F2>& rc) {
+  constexpr int cls = speed2_of(T);
+  const float rB = K.refB[cls].v.x, dR = cls == 0 ? K.dref[0].v.x : 0.0f;
+  const F2 fstar = f[T];
+  F2 outr, q;
+  if (T == REST) {
+    outr = rc.frac * fstar;
+    q = rc.frac;
+  } else {
+    const F2 cn = cdot<T>(rc.n0, rc.n1, rc.n2);
+    outr = fma_(rc.frac, fstar, rc.rc[cls] * cn);
+    q = select_(rc.has_n, sat_(outr * rcp_(fstar)), rc.frac);
+  }
+  const F2 outb = fstar - outr;
+  if (!odd) {
+    st.store_p(base, opp_of(T), rB, dR, outr, outb, fstar, q);
+  } else {
+    int64_t n0, n1;
+    int d0, d1;
+    m0.push<T>(n0, d0);
+    m1.push<T>(n1, d1);
+    st.store_s(n0, d0, rB, dR, outr.v.x, outb.v.x, fstar.v.x, q.v.x);
+    st.store_s(n1, d1, rB, dR, outr.v.y, outb.v.y, fstar.v.y, q.v.y);
+  }
+}
+
+template <int T, class Store>
+struct EmitLoop2 {
+  __device__ __forceinline__ static void run(const Store& st, const KConst<F2>& K, int64_t base, const NodeMap& m0,
+                                             const NodeMap& m1, bool odd, const F2* f, const Recol<F2>& rc) {
+    emit2<T>(st, K, base, m0, m1, odd, f, rc);
+    EmitLoop2<T + 1, Store>::run(st, K, base, m0, m1, odd, f, rc);
+  }
+};
+template <class Store>
+struct EmitLoop2<27, Store> {
+  __device__ __forceinline__ static void run(const Store&, const KConst<F2>&, int64_t, const NodeMap&,
+                                             const NodeMap&, bool, const F2*, const Recol<F2>&) {}
+};
+
+template <class Store, int MINB>
+__global__ void __launch_bounds__(PTHREADS, MINB)
+    k_collide_stream2(Store st, const __grid_constant__ Geom G, const __grid_constant__ KConst<F2> K, int odd,
+                      const float2* __restrict__ dens, const long long* __restrict__ step_counter) {
+  __shared__ float2 tile[TILE];
+  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * PY, z0 = blockIdx.z * PZ;
+  const int xa = x0 + 2 * threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
+  const bool active = xa < G.nx && y < G.ny && z < G.nz;  // nx even: xa + 1 < nx as well
+
+  const int64_t base = snode(G, xa, y, z);
+  NodeMap m0, m1;
+  F2 fr[27], ft[27];
+  if (active) {
+    if (!odd) {
+#pragma unroll
+      for (int t = 0; t < 27; ++t) {
+        st.load_p(base, t, K.refB[speed2_of(t)].v.x, speed2_of(t) == 0 ? K.dref[0].v.x : 0.0f, fr[t], ft[t]);
+      }
+    } else {
+      m0.init(G, xa, y, z);
+      m1.init(G, xa + 1, y, z);
+#pragma unroll
+      for (int t = 0; t < 27; ++t) {
+        int64_t n0, n1;
+        int d0, d1;
+        slot_of(m0, 1, t, n0, d0);
+        slot_of(m1, 1, t, n1, d1);
+        const float rB = K.refB[speed2_of(t)].v.x, dR = speed2_of(t) == 0 ? K.dref[0].v.x : 0.0f;
+        st.load_s(n0, d0, rB, dR, fr[t].v.x, ft[t].v.x);
+        st.load_s(n1, d1, rB, dR, fr[t].v.y, ft[t].v.y);
+      }
+    }
+  }
+
+  // halo tile of (rho, phi): warp w fills rows w, w+4, ... of the TY*TZ rows
+  {
+    const int tid = threadIdx.x + PX * (threadIdx.y + PY * threadIdx.z);
+    const int warp = tid >> 5, lane = tid & 31;
+    const int xl = wrap_or_clamp(x0 + lane - 1, G.nx, G.bc[0], G.bc[1]);
+    const int xr = wrap_or_clamp(x0 + lane + 31, G.nx, G.bc[0], G.bc[1]);
+    const int cxl = xl < G.nx ? xl : G.nx - 1, cxr = xr < G.nx ? xr : G.nx - 1;
+#pragma unroll
+    for (int k = 0; k < (TY * TZ + PTHREADS / 32 - 1) / (PTHREADS / 32); ++k) {
+      const int row = warp + k * (PTHREADS / 32);
+      if (row < TY * TZ) {
+        const int ty = row % TY, tz = row / TY;
+        const int gy = wrap_or_clamp(y0 + ty - 1, G.ny, G.bc[2], G.bc[3]);
+        const int gz = wrap_or_clamp(z0 + tz - 1, G.nz, G.bc[4], G.bc[5]);
+        const int64_t rbase = (int64_t)G.nx * ((int64_t)(gy < G.ny ? gy : G.ny - 1) +
+                                                (int64_t)G.ny * (gz < G.nz ? gz : G.nz - 1));
+        tile[row * TX + lane] = dens[rbase + cxl];
+        if (lane < TX - 32) tile[row * TX + 32 + lane] = dens[rbase + cxr];
+      }
+    }
+  }
+  __syncthreads();
+  if (!active) return;
+
+  F2 gphi[3] = {F2(0.0f), F2(0.0f), F2(0.0f)}, grho[3] = {F2(0.0f), F2(0.0f), F2(0.0f)};
+  const int lx = 2 * threadIdx.x + 1, ly = threadIdx.y + 1, lz = threadIdx.z + 1;
+#pragma unroll
+  for (int t = 0; t < 27; ++t) {
+    if (t == REST) continue;
+    const int o = (lx + cx_of(t)) + TX * ((ly + cy_of(t)) + TY * (lz + cz_of(t)));
+    const float2 v0 = tile[o], v1 = tile[o + 1];
+    const F2 w3 = F2(float(3.0 * weight_of(t)));
+    const F2 a = w3 * F2(v0.y, v1.y), b = w3 * F2(v0.x, v1.x);
+    if (cx_of(t) != 0) { gphi[0] = fma_(F2(float(cx_of(t))), a, gphi[0]); grho[0] = fma_(F2(float(cx_of(t))), b, grho[0]); }
+    if (cy_of(t) != 0) { gphi[1] = fma_(F2(float(cy_of(t))), a, gphi[1]); grho[1] = fma_(F2(float(cy_of(t))), b, grho[1]); }
+    if (cz_of(t) != 0) { gphi[2] = fma_(F2(float(cz_of(t))), a, gphi[2]); grho[2] = fma_(F2(float(cz_of(t))), b, grho[2]); }
+  }
+
+  F2 f[27];
+  Recol<F2> rc = collide(K, fr, ft, gphi, grho, f);
+  if (z == 0 && G.inflow) {
+    // Dirichlet inlet nodes (Sec. IV.A) replace the collision result lane by lane
+#pragma unroll
+    for (int lane = 0; lane < 2; ++lane) {
+      if (is_inlet(G, xa + lane, y, z)) {
+        float fin[27];
+        KConst<float> Ks;
+        Ks.u_j0 = K.u_j0;
+        Ks.noise_frac = K.noise_frac;
+        Ks.seed = K.seed;
+        Ks.rho_r0_d = K.rho_r0_d;
+        Ks.alpha_r_d = K.alpha_r_d;
+        inlet_state(Ks, dnode(G, xa + lane, y, z), (int64_t)*step_counter, fin);
+#pragma unroll
+        for (int t = 0; t < 27; ++t) {
+          if (lane == 0) f[t].v.x = fin[t]; else f[t].v.y = fin[t];
+        }
+        if (lane == 0) {
+          rc.frac.v.x = 1.0f; rc.n0.v.x = rc.n1.v.x = rc.n2.v.x = 0.0f; rc.has_n.x = false;
+          rc.rc[1].v.x = rc.rc[2].v.x = rc.rc[3].v.x = 0.0f;
+        } else {
+          rc.frac.v.y = 1.0f; rc.n0.v.y = rc.n1.v.y = rc.n2.v.y = 0.0f; rc.has_n.y = false;
+          rc.rc[1].v.y = rc.rc[2].v.y = rc.rc[3].v.y = 0.0f;
+        }
+      }
+    }
+  }
+  EmitLoop2<0, Store>::run(st, K, base, m0, m1, odd != 0, f, rc);
 }
 
 // write one population pair at (node, dir) of a runtime direction (I/O kernels)
@@ -650,7 +968,13 @@ __global__ void k_outflow(Store st, Geom G, const __grid_constant__ KConst<typen
   below.init(G, x, y, G.nz - 2);
   here.init(G, x, y, G.nz - 1);
   R fr[27], fb[27];
-  load_node(st, K, below, layout, fr, fb);
+#pragma unroll
+  for (int t = 0; t < 27; ++t) {
+    int64_t node;
+    int dir;
+    slot_of(below, layout, t, node, dir);
+    st.load_rb(node, dir, speed2_of(t), K, fr[t], fb[t]);
+  }
   R rho = R(0), mz = R(0);
 #pragma unroll
   for (int t = 0; t < 27; ++t) {
@@ -722,7 +1046,7 @@ __global__ void k_get_pop(Store st, Geom G, const __grid_constant__ KConst<typen
   const int t = paper_to_tensor(pdir);
   slot_of(nm, layout, t, node, dir);
   R fr, fb;
-  st.load(node, dir, speed2_of(t), K, fr, fb);
+  st.load_rb(node, dir, speed2_of(t), K, fr, fb);
   out_r[n] = (double)fr;
   out_b[n] = (double)fb;
 }
@@ -758,7 +1082,7 @@ __global__ void k_top_from_state(Store st, Geom G, const __grid_constant__ KCons
     int dir;
     slot_of(nm, layout, t, node, dir);
     R fr, fb;
-    st.load(node, dir, speed2_of(t), K, fr, fb);
+    st.load_rb(node, dir, speed2_of(t), K, fr, fb);
     top[(int64_t)t * Pn + pp] = fr;
     top[(int64_t)(27 + t) * Pn + pp] = fb;
   }
@@ -776,7 +1100,13 @@ __global__ void k_macro(Store st, Geom G, const __grid_constant__ KConst<typenam
   NodeMap nm;
   nm.init(G, x, y, z);
   R fr[27], fb[27];
-  load_node(st, K, nm, layout, fr, fb);
+#pragma unroll
+  for (int t = 0; t < 27; ++t) {
+    int64_t node;
+    int dir;
+    slot_of(nm, layout, t, node, dir);
+    st.load_rb(node, dir, speed2_of(t), K, fr[t], fb[t]);
+  }
   double r = 0.0, b = 0.0, j[3] = {0.0, 0.0, 0.0};
 #pragma unroll
   for (int t = 0; t < 27; ++t) {

@@ -7,14 +7,15 @@
 // of the printed M in App. A) is used only at the C ABI.
 //
 // Moments.  The raw moments R_abc = sum_i cx^a cy^b cz^c f_i (a,b,c in 0..2)
-// follow from three one-dimensional 3-point transforms (one per axis).  The
-// moments m_1..m_27 of Eq. (momentSet) are sparse integer combinations of the
-// R_abc (moment_forward).  Because the rows of M are mutually orthogonal,
-// M^-1 = M^T diag(1/|M_j|^2), so the way back is the transpose of the same two
-// steps (moment_adjoint, then the transposed 1D transforms) scaled by the
-// inverse row norms; the kernels never hold a dense 27x27 matrix.
+// follow from three one-dimensional 3-point transforms (one per axis,
+// raw_forward; raw_inverse undoes them).  The moments m_1..m_27 of
+// Eq. (momentSet) are sparse integer combinations of the R_abc
+// (moment_forward, M = T V3), and T has a sparse block inverse
+// (moment_inverse_add), so the kernels never hold a dense 27x27 matrix.
 #pragma once
 #include <stdint.h>
+
+#include "lbm_f2.cuh"
 
 namespace lbmk {
 
@@ -85,6 +86,26 @@ __host__ __device__ inline int kslot_of(int j) {
   return 27;
 }
 
+// c_T . (a0, a1, a2) with the zero components of c_T left out (IEEE arithmetic
+// cannot drop a product with zero on its own).
+template <int C, typename R>
+__host__ __device__ __forceinline__ R signed_(R a) {
+  if constexpr (C > 0) return a;
+  else return -a;
+}
+template <int T, typename R>
+__host__ __device__ __forceinline__ R cdot(R a0, R a1, R a2) {
+  constexpr int c0 = cx_of(T), c1 = cy_of(T), c2 = cz_of(T);
+  if constexpr (c0 != 0 && c1 != 0 && c2 != 0) return signed_<c0>(a0) + signed_<c1>(a1) + signed_<c2>(a2);
+  else if constexpr (c0 != 0 && c1 != 0) return signed_<c0>(a0) + signed_<c1>(a1);
+  else if constexpr (c0 != 0 && c2 != 0) return signed_<c0>(a0) + signed_<c2>(a2);
+  else if constexpr (c1 != 0 && c2 != 0) return signed_<c1>(a1) + signed_<c2>(a2);
+  else if constexpr (c0 != 0) return signed_<c0>(a0);
+  else if constexpr (c1 != 0) return signed_<c1>(a1);
+  else if constexpr (c2 != 0) return signed_<c2>(a2);
+  else return R(0);
+}
+
 // ---------------------------------------------------------------------------
 // raw moments: in-place 1D 3-point transforms along x, y and z.
 // (f_-, f_0, f_+) -> (f_- + f_0 + f_+, f_+ - f_-, f_+ + f_-): orders 0, 1, 2.
@@ -95,16 +116,6 @@ __host__ __device__ __forceinline__ void tri_forward(R& a, R& b, R& c) {
   b = d;
   c = s;
 }
-// transpose of tri_forward: (k0, k1, k2) -> (k0 - k1 + k2, k0, k0 + k1 + k2).
-template <typename R>
-__host__ __device__ __forceinline__ void tri_adjoint(R& a, R& b, R& c) {
-  R k0 = a, k1 = b, k2 = c;
-  R s = k0 + k2;
-  a = s - k1;
-  b = k0;
-  c = s + k1;
-}
-
 template <typename R>
 __host__ __device__ __forceinline__ void raw_forward(R v[27]) {
 #pragma unroll
@@ -118,17 +129,28 @@ __host__ __device__ __forceinline__ void raw_forward(R v[27]) {
   for (int l = 0; l < 9; ++l) tri_forward(v[l], v[l + 9], v[l + 18]);  // z
 }
 
+// inverse of tri_forward: (k0, k1, k2) -> ((k2 - k1)/2, k0 - k2, (k2 + k1)/2).
 template <typename R>
-__host__ __device__ __forceinline__ void raw_adjoint(R v[27]) {
+__host__ __device__ __forceinline__ void tri_inverse(R& a, R& b, R& c) {
+  const R k0 = a, k1 = b, k2 = c;
+  const R h2 = R(0.5) * k2;
+  a = fma_(R(-0.5), k1, h2);
+  b = k0 - k2;
+  c = fma_(R(0.5), k1, h2);
+}
+
+// populations from raw moments: the inverse of raw_forward (z, then y, then x).
+template <typename R>
+__host__ __device__ __forceinline__ void raw_inverse(R v[27]) {
 #pragma unroll
-  for (int l = 0; l < 9; ++l) tri_adjoint(v[l], v[l + 9], v[l + 18]);
+  for (int l = 0; l < 9; ++l) tri_inverse(v[l], v[l + 9], v[l + 18]);
 #pragma unroll
   for (int l = 0; l < 9; ++l) {
     int base = (l % 3) + 9 * (l / 3);
-    tri_adjoint(v[base], v[base + 3], v[base + 6]);
+    tri_inverse(v[base], v[base + 3], v[base + 6]);
   }
 #pragma unroll
-  for (int l = 0; l < 9; ++l) tri_adjoint(v[3 * l + 0], v[3 * l + 1], v[3 * l + 2]);
+  for (int l = 0; l < 9; ++l) tri_inverse(v[3 * l + 0], v[3 * l + 1], v[3 * l + 2]);
 }
 
 #define LBMK_R(a, b, c) r[(a) + 3 * (b) + 9 * (c)]
@@ -143,67 +165,113 @@ __host__ __device__ __forceinline__ void moment_forward(const R r[27], R m[27]) 
   m[1] = LBMK_R(1, 0, 0);
   m[2] = LBMK_R(0, 1, 0);
   m[3] = LBMK_R(0, 0, 1);
-  m[4] = S2 - R(2) * LBMK_R(0, 0, 0);                                        // -2<1> + <|c|^2>
-  m[5] = R(2) * LBMK_R(2, 0, 0) - LBMK_R(0, 2, 0) - LBMK_R(0, 0, 2);        // 2<cx^2> - <cy^2+cz^2>
+  m[4] = fma_(R(-2), LBMK_R(0, 0, 0), S2);                                   // -2<1> + <|c|^2>
+  m[5] = fma_(R(3), LBMK_R(2, 0, 0), -S2);                                   // 2<cx^2> - <cy^2+cz^2>
   m[6] = LBMK_R(0, 2, 0) - LBMK_R(0, 0, 2);                                  // <cy^2 - cz^2>
   m[7] = LBMK_R(1, 1, 0);                                                    // <cx cy>
   m[8] = LBMK_R(0, 1, 1);                                                    // <cy cz>
   m[9] = LBMK_R(1, 0, 1);                                                    // <cz cx>
-  m[10] = R(3) * (LBMK_R(1, 2, 0) + LBMK_R(1, 0, 2)) - R(4) * LBMK_R(1, 0, 0);
-  m[11] = R(3) * (LBMK_R(0, 1, 2) + LBMK_R(2, 1, 0)) - R(4) * LBMK_R(0, 1, 0);
-  m[12] = R(3) * (LBMK_R(2, 0, 1) + LBMK_R(0, 2, 1)) - R(4) * LBMK_R(0, 0, 1);
-  m[13] = R(4) * LBMK_R(1, 0, 0) - R(6) * (LBMK_R(1, 2, 0) + LBMK_R(1, 0, 2)) + R(9) * LBMK_R(1, 2, 2);
-  m[14] = R(4) * LBMK_R(0, 1, 0) - R(6) * (LBMK_R(0, 1, 2) + LBMK_R(2, 1, 0)) + R(9) * LBMK_R(2, 1, 2);
-  m[15] = R(4) * LBMK_R(0, 0, 1) - R(6) * (LBMK_R(2, 0, 1) + LBMK_R(0, 2, 1)) + R(9) * LBMK_R(2, 2, 1);
-  m[16] = R(4) * (LBMK_R(0, 0, 0) - S2) + R(3) * S4;                                         // 4<1-|c|^2> + 3<..>
-  m[17] = R(-8) * LBMK_R(0, 0, 0) + R(12) * S2 - R(18) * S4 + R(27) * LBMK_R(2, 2, 2);
-  m[18] = R(2) * (LBMK_R(0, 0, 2) + LBMK_R(0, 2, 0)) + R(3) * (LBMK_R(2, 2, 0) + LBMK_R(2, 0, 2)) -
-          R(4) * LBMK_R(2, 0, 0) - R(6) * LBMK_R(0, 2, 2);
-  m[19] = R(2) * (LBMK_R(0, 0, 2) - LBMK_R(0, 2, 0)) + R(3) * (LBMK_R(2, 2, 0) - LBMK_R(2, 0, 2));
-  m[20] = R(3) * LBMK_R(1, 1, 2) - R(2) * LBMK_R(1, 1, 0);
-  m[21] = R(3) * LBMK_R(2, 1, 1) - R(2) * LBMK_R(0, 1, 1);
-  m[22] = R(3) * LBMK_R(1, 2, 1) - R(2) * LBMK_R(1, 0, 1);
+  const R Ax = LBMK_R(1, 2, 0) + LBMK_R(1, 0, 2), Ay = LBMK_R(0, 1, 2) + LBMK_R(2, 1, 0);
+  const R Az = LBMK_R(2, 0, 1) + LBMK_R(0, 2, 1);
+  m[10] = fma_(R(3), Ax, R(-4) * LBMK_R(1, 0, 0));
+  m[11] = fma_(R(3), Ay, R(-4) * LBMK_R(0, 1, 0));
+  m[12] = fma_(R(3), Az, R(-4) * LBMK_R(0, 0, 1));
+  m[13] = fma_(R(9), LBMK_R(1, 2, 2), fma_(R(-6), Ax, R(4) * LBMK_R(1, 0, 0)));
+  m[14] = fma_(R(9), LBMK_R(2, 1, 2), fma_(R(-6), Ay, R(4) * LBMK_R(0, 1, 0)));
+  m[15] = fma_(R(9), LBMK_R(2, 2, 1), fma_(R(-6), Az, R(4) * LBMK_R(0, 0, 1)));
+  m[16] = fma_(R(3), S4, R(4) * (LBMK_R(0, 0, 0) - S2));                                     // 4<1-|c|^2> + 3<..>
+  m[17] = fma_(R(27), LBMK_R(2, 2, 2), fma_(R(-18), S4, fma_(R(12), S2, R(-8) * LBMK_R(0, 0, 0))));
+  m[18] = fma_(R(2), LBMK_R(0, 0, 2) + LBMK_R(0, 2, 0),
+               fma_(R(3), LBMK_R(2, 2, 0) + LBMK_R(2, 0, 2), fma_(R(-4), LBMK_R(2, 0, 0), R(-6) * LBMK_R(0, 2, 2))));
+  m[19] = fma_(R(2), LBMK_R(0, 0, 2) - LBMK_R(0, 2, 0), R(3) * (LBMK_R(2, 2, 0) - LBMK_R(2, 0, 2)));
+  m[20] = fma_(R(3), LBMK_R(1, 1, 2), R(-2) * LBMK_R(1, 1, 0));
+  m[21] = fma_(R(3), LBMK_R(2, 1, 1), R(-2) * LBMK_R(0, 1, 1));
+  m[22] = fma_(R(3), LBMK_R(1, 2, 1), R(-2) * LBMK_R(1, 0, 1));
   m[23] = LBMK_R(1, 2, 0) - LBMK_R(1, 0, 2);
   m[24] = LBMK_R(0, 1, 2) - LBMK_R(2, 1, 0);
   m[25] = LBMK_R(2, 0, 1) - LBMK_R(0, 2, 1);
   m[26] = LBMK_R(1, 1, 1);
 }
 
-// r = T^T y: the transpose of moment_forward (T maps raw moments to Eq.
-// momentSet moments), over the moments 5..27 only (y[0..3] are ignored).
+// r += T^-1 y for a change y of the moments 5..27 (y[0..3] must be zero): the
+// inverse of the sparse map of moment_forward, block by block (scalars;
+// x-, y-, z-vectors; the three off-diagonal pairs; c_x c_y c_z).
 template <typename R>
-__host__ __device__ __forceinline__ void moment_adjoint(const R y[27], R r[27]) {
-  const R a16 = R(4) * y[16] - R(8) * y[17];          // common to R000
-  const R s2 = y[4] - R(4) * y[16] + R(12) * y[17];   // common to R200, R020, R002
-  const R s4 = R(3) * y[16] - R(18) * y[17];          // common to R220, R022, R202
-  LBMK_R(0, 0, 0) = a16 - R(2) * y[4];
-  LBMK_R(1, 0, 0) = R(4) * (y[13] - y[10]);
-  LBMK_R(0, 1, 0) = R(4) * (y[14] - y[11]);
-  LBMK_R(0, 0, 1) = R(4) * (y[15] - y[12]);
-  LBMK_R(2, 0, 0) = s2 + R(2) * y[5] - R(4) * y[18];
-  LBMK_R(0, 2, 0) = s2 - y[5] + y[6] + R(2) * y[18] - R(2) * y[19];
-  LBMK_R(0, 0, 2) = s2 - y[5] - y[6] + R(2) * y[18] + R(2) * y[19];
-  LBMK_R(1, 1, 0) = y[7] - R(2) * y[20];
-  LBMK_R(0, 1, 1) = y[8] - R(2) * y[21];
-  LBMK_R(1, 0, 1) = y[9] - R(2) * y[22];
-  LBMK_R(1, 2, 0) = R(3) * y[10] - R(6) * y[13] + y[23];
-  LBMK_R(1, 0, 2) = R(3) * y[10] - R(6) * y[13] - y[23];
-  LBMK_R(0, 1, 2) = R(3) * y[11] - R(6) * y[14] + y[24];
-  LBMK_R(2, 1, 0) = R(3) * y[11] - R(6) * y[14] - y[24];
-  LBMK_R(2, 0, 1) = R(3) * y[12] - R(6) * y[15] + y[25];
-  LBMK_R(0, 2, 1) = R(3) * y[12] - R(6) * y[15] - y[25];
-  LBMK_R(1, 2, 2) = R(9) * y[13];
-  LBMK_R(2, 1, 2) = R(9) * y[14];
-  LBMK_R(2, 2, 1) = R(9) * y[15];
-  LBMK_R(2, 2, 0) = s4 + R(3) * y[18] + R(3) * y[19];
-  LBMK_R(0, 2, 2) = s4 - R(6) * y[18];
-  LBMK_R(2, 0, 2) = s4 + R(3) * y[18] - R(3) * y[19];
-  LBMK_R(2, 2, 2) = R(27) * y[17];
-  LBMK_R(1, 1, 2) = R(3) * y[20];
-  LBMK_R(2, 1, 1) = R(3) * y[21];
-  LBMK_R(1, 2, 1) = R(3) * y[22];
-  LBMK_R(1, 1, 1) = y[26];
+__host__ __device__ __forceinline__ void moment_inverse_add(const R y[27], R r[27]) {
+  // scalar block (moments 1, 5, 6, 7, 17, 18, 19, 20 <-> R000, R200, R020, R002, R220, R202, R022, R222)
+  const R dS2 = y[4];                                            // change of R200 + R020 + R002
+  const R dS4 = fma_(R(4.0 / 3.0), dS2, R(1.0 / 3.0) * y[16]);    // change of R220 + R202 + R022
+  const R d200 = R(1.0 / 3.0) * (y[5] + dS2);
+  const R d022 = R(1.0 / 9.0) * fma_(R(2), dS2, fma_(R(-6), d200, fma_(R(3), dS4, -y[18])));
+  const R dsum = dS4 - d022;                                      // change of R220 + R202
+  const R ddif = R(1.0 / 3.0) * fma_(R(2), y[6], y[19]);          // change of R220 - R202
+  const R e = dS2 - d200;
+  LBMK_R(2, 0, 0) += d200;
+  LBMK_R(0, 2, 0) = fma_(R(0.5), e + y[6], LBMK_R(0, 2, 0));
+  LBMK_R(0, 0, 2) = fma_(R(0.5), e - y[6], LBMK_R(0, 0, 2));
+  LBMK_R(0, 2, 2) += d022;
+  LBMK_R(2, 2, 0) = fma_(R(0.5), dsum + ddif, LBMK_R(2, 2, 0));
+  LBMK_R(2, 0, 2) = fma_(R(0.5), dsum - ddif, LBMK_R(2, 0, 2));
+  LBMK_R(2, 2, 2) = fma_(R(1.0 / 27.0), fma_(R(-12), dS2, fma_(R(18), dS4, y[17])), LBMK_R(2, 2, 2));
+  // vector blocks (moments 2/11/14/24, 3/12/15/25, 4/13/16/26)
+  const R vx = R(1.0 / 3.0) * y[10], vy = R(1.0 / 3.0) * y[11], vz = R(1.0 / 3.0) * y[12];
+  LBMK_R(1, 2, 0) = fma_(R(0.5), vx + y[23], LBMK_R(1, 2, 0));
+  LBMK_R(1, 0, 2) = fma_(R(0.5), vx - y[23], LBMK_R(1, 0, 2));
+  LBMK_R(1, 2, 2) = fma_(R(1.0 / 9.0), fma_(R(2), y[10], y[13]), LBMK_R(1, 2, 2));
+  LBMK_R(0, 1, 2) = fma_(R(0.5), vy + y[24], LBMK_R(0, 1, 2));
+  LBMK_R(2, 1, 0) = fma_(R(0.5), vy - y[24], LBMK_R(2, 1, 0));
+  LBMK_R(2, 1, 2) = fma_(R(1.0 / 9.0), fma_(R(2), y[11], y[14]), LBMK_R(2, 1, 2));
+  LBMK_R(2, 0, 1) = fma_(R(0.5), vz + y[25], LBMK_R(2, 0, 1));
+  LBMK_R(0, 2, 1) = fma_(R(0.5), vz - y[25], LBMK_R(0, 2, 1));
+  LBMK_R(2, 2, 1) = fma_(R(1.0 / 9.0), fma_(R(2), y[12], y[15]), LBMK_R(2, 2, 1));
+  // off-diagonal pairs (moments 8/21, 9/22, 10/23) and moment 27
+  LBMK_R(1, 1, 0) += y[7];
+  LBMK_R(1, 1, 2) = fma_(R(1.0 / 3.0), fma_(R(2), y[7], y[20]), LBMK_R(1, 1, 2));
+  LBMK_R(0, 1, 1) += y[8];
+  LBMK_R(2, 1, 1) = fma_(R(1.0 / 3.0), fma_(R(2), y[8], y[21]), LBMK_R(2, 1, 1));
+  LBMK_R(1, 0, 1) += y[9];
+  LBMK_R(1, 2, 1) = fma_(R(1.0 / 3.0), fma_(R(2), y[9], y[22]), LBMK_R(1, 2, 1));
+  LBMK_R(1, 1, 1) += y[26];
 }
+
+// Raw moments of g_i = w_i Q(c_i), Q(c) = C0 + c.V + c.S.c with S symmetric
+// (S = {Sxx, Syy, Szz, Sxy, Syz, Sxz}): products of the D1Q3 weight moments
+// sum W(c) c^k = 1, 0, 1/3, 0, 1/3 (k = 0..4).  r_abc += sign * R_abc[g] for
+// every raw moment except R000 (whose change the caller fixes).
+template <typename R>
+__host__ __device__ __forceinline__ void closed_raw_add(R r[27], R sign, R C0, const R V[3], const R S[6]) {
+  const R t3 = R(1.0 / 3.0) * sign, t9 = R(1.0 / 9.0) * sign, t27 = R(1.0 / 27.0) * sign;
+  const R Sxx = S[0], Syy = S[1], Szz = S[2];
+  const R a = C0 + Sxx, b = C0 + Syy, c = C0 + Szz, yz = Syy + Szz, xz = Sxx + Szz, xy = Sxx + Syy;
+  LBMK_R(1, 0, 0) = fma_(t3, V[0], LBMK_R(1, 0, 0));
+  LBMK_R(0, 1, 0) = fma_(t3, V[1], LBMK_R(0, 1, 0));
+  LBMK_R(0, 0, 1) = fma_(t3, V[2], LBMK_R(0, 0, 1));
+  LBMK_R(2, 0, 0) = fma_(t3, a, fma_(t9, yz, LBMK_R(2, 0, 0)));
+  LBMK_R(0, 2, 0) = fma_(t3, b, fma_(t9, xz, LBMK_R(0, 2, 0)));
+  LBMK_R(0, 0, 2) = fma_(t3, c, fma_(t9, xy, LBMK_R(0, 0, 2)));
+  LBMK_R(2, 2, 0) = fma_(t9, a + Syy, fma_(t27, Szz, LBMK_R(2, 2, 0)));
+  LBMK_R(2, 0, 2) = fma_(t9, a + Szz, fma_(t27, Syy, LBMK_R(2, 0, 2)));
+  LBMK_R(0, 2, 2) = fma_(t9, b + Szz, fma_(t27, Sxx, LBMK_R(0, 2, 2)));
+  LBMK_R(2, 2, 2) = fma_(t27, a + yz, LBMK_R(2, 2, 2));
+  const R v0 = t9 * V[0], v1 = t9 * V[1], v2 = t9 * V[2];
+  LBMK_R(1, 2, 0) += v0;
+  LBMK_R(1, 0, 2) += v0;
+  LBMK_R(1, 2, 2) = fma_(t27, V[0], LBMK_R(1, 2, 2));
+  LBMK_R(2, 1, 0) += v1;
+  LBMK_R(0, 1, 2) += v1;
+  LBMK_R(2, 1, 2) = fma_(t27, V[1], LBMK_R(2, 1, 2));
+  LBMK_R(2, 0, 1) += v2;
+  LBMK_R(0, 2, 1) += v2;
+  LBMK_R(2, 2, 1) = fma_(t27, V[2], LBMK_R(2, 2, 1));
+  const R u9 = R(2) * t9, u27 = R(2) * t27;
+  LBMK_R(1, 1, 0) = fma_(u9, S[3], LBMK_R(1, 1, 0));
+  LBMK_R(1, 1, 2) = fma_(u27, S[3], LBMK_R(1, 1, 2));
+  LBMK_R(0, 1, 1) = fma_(u9, S[4], LBMK_R(0, 1, 1));
+  LBMK_R(2, 1, 1) = fma_(u27, S[4], LBMK_R(2, 1, 1));
+  LBMK_R(1, 0, 1) = fma_(u9, S[5], LBMK_R(1, 0, 1));
+  LBMK_R(1, 2, 1) = fma_(u27, S[5], LBMK_R(1, 2, 1));
+}
+
 #undef LBMK_R
 
 // Full 27x27 transformation matrix as the kernels apply it, column t = tensor

@@ -14,17 +14,20 @@ template <class Store>
 struct StoreTraits;
 template <>
 struct StoreTraits<PlainStore<double>> {
-  static constexpr int minb = 1;
+  static constexpr bool paired = false;
+  static constexpr int minb = 1, minb2 = 1;
   static PlainStore<double> make(void* p, const Geom& G) { return {static_cast<double*>(p), G.Ns}; }
 };
 template <>
 struct StoreTraits<PlainStore<float>> {
-  static constexpr int minb = 2;
+  static constexpr bool paired = true;
+  static constexpr int minb = 3, minb2 = 2;
   static PlainStore<float> make(void* p, const Geom& G) { return {static_cast<float*>(p), G.Ns}; }
 };
 template <bool B>
 struct StoreTraits<PackedStore<B>> {
-  static constexpr int minb = 2;
+  static constexpr bool paired = true;
+  static constexpr int minb = 3, minb2 = 2;
   static PackedStore<B> make(void* p, const Geom& G) { return {static_cast<uint32_t*>(p), G.Ns}; }
 };
 
@@ -42,7 +45,14 @@ struct Launch {
     return cudaGetLastError();
   }
   static cudaError_t collide(void* pop, const Geom& G, const Phys& P, int odd, const void* dens, const long long* step,
-                             cudaStream_t s) {
+                             int variant, cudaStream_t s) {
+    if constexpr (Tr::paired) {
+      if (variant == 2) {
+        k_collide_stream2<Store, Tr::minb2><<<grid3(G), dim3(PX, PY, PZ), 0, s>>>(
+            Tr::make(pop, G), G, make_kconst<F2>(P), odd, static_cast<const float2*>(dens), step);
+        return cudaGetLastError();
+      }
+    }
     k_collide_stream<Store, Tr::minb><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(Tr::make(pop, G), G, kc(P), odd,
                                                                             static_cast<const DT*>(dens), step);
     return cudaGetLastError();
@@ -81,11 +91,6 @@ struct Launch {
     k_macro<Store><<<blocks1(N, 256), 256, 0, s>>>(Tr::make(pop, G), G, kc(P), layout, rr, rb, u);
     return cudaGetLastError();
   }
-  static int collide_regs() {
-    cudaFuncAttributes a;
-    if (cudaFuncGetAttributes(&a, k_collide_stream<Store, Tr::minb>) != cudaSuccess) return -1;
-    return a.numRegs;
-  }
   static const KernelSet* table() {
     static const KernelSet ks = {
         sizeof(typename std::conditional<std::is_same<Store, PlainStore<double>>::value, double,
@@ -94,7 +99,7 @@ struct Launch {
         (std::is_same<Store, PlainStore<double>>::value || std::is_same<Store, PlainStore<float>>::value) ? 2 : 1,
         sizeof(DT),
         sizeof(R),
-        &density, &collide, &outflow, &init, &get_pop, &set_pop, &top_from_state, &macro, &collide_regs};
+        &density, &collide, &outflow, &init, &get_pop, &set_pop, &top_from_state, &macro, Tr::paired};
     return &ks;
   }
 };

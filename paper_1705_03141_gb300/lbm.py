@@ -49,6 +49,7 @@ class Params(ctypes.Structure):
         ("cuda_stream", ctypes.c_void_p),
         ("workspace", ctypes.c_void_p),
         ("workspace_bytes", ctypes.c_size_t),
+        ("variant", ctypes.c_int),
     ]
 
 
@@ -95,7 +96,7 @@ def library():
     return _lib
 
 
-def _params_struct(p: dict, storage: int, stream=None, workspace=None, workspace_bytes=0) -> Params:
+def _params_struct(p: dict, storage: int, stream=None, workspace=None, workspace_bytes=0, variant=0) -> Params:
     s = Params()
     s.rho_r0, s.rho_b0 = float(p["rho_r0"]), float(p["rho_b0"])
     s.nu_r, s.nu_b = float(p["nu_r"]), float(p["nu_b"])
@@ -113,6 +114,7 @@ def _params_struct(p: dict, storage: int, stream=None, workspace=None, workspace
     s.cuda_stream = stream
     s.workspace = workspace
     s.workspace_bytes = int(workspace_bytes)
+    s.variant = int(variant)
     return s
 
 
@@ -178,7 +180,7 @@ class Lattice:
     current CUDA stream at creation time (``set_stream`` changes it).
     """
 
-    def __init__(self, shape, params: dict, storage="f32", device=None, stream=None):
+    def __init__(self, shape, params: dict, storage="f32", device=None, stream=None, variant=0):
         import torch
 
         self.nx, self.ny, self.nz = (int(v) for v in shape)
@@ -189,12 +191,12 @@ class Lattice:
         with torch.cuda.device(self.device):
             st = torch.cuda.current_stream(self.device) if stream is None else stream
             self.stream = st
-            probe = _params_struct(self.params, self.storage)
+            probe = _params_struct(self.params, self.storage, variant=variant)
             nbytes = ctypes.c_size_t()
             _check(lib.lbm_workspace_size(self.nx, self.ny, self.nz, ctypes.byref(probe), ctypes.byref(nbytes)), None)
             self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
             ps = _params_struct(self.params, self.storage, stream=st.cuda_stream,
-                                workspace=self.workspace.data_ptr(), workspace_bytes=nbytes.value)
+                                workspace=self.workspace.data_ptr(), workspace_bytes=nbytes.value, variant=variant)
             h = ctypes.c_void_p()
             _check(lib.lbm_create(self.nx, self.ny, self.nz, ctypes.byref(ps), ctypes.byref(h)), None)
         self._h = h

@@ -17,9 +17,9 @@ pytestmark = pytest.mark.gpu
 CASES = {name: (w, u) for name, w, u in L.parity_cases()}
 
 
-def _pair(work, u_amp, storage, seed=11):
+def _pair(work, u_amp, storage, seed=11, variant=0):
     rr, rb, u = L.initial_fields(work, seed=seed, u_amp=u_amp)
-    lat = pkg.Lattice(work["shape"], work["params"], storage=storage)
+    lat = pkg.Lattice(work["shape"], work["params"], storage=storage, variant=variant)
     lat.init_fields(rr, rb, u)
     orc = oracle.Oracle(work["shape"], work["params"])
     orc.init_fields(rr, rb, u)
@@ -47,13 +47,18 @@ def test_fp64_matches_oracle_100_steps(cuda, name):
     lat.close()
 
 
-@pytest.mark.parametrize("name", list(CASES))
-def test_fp32_matches_oracle(cuda, name):
+def _variants(name):
+    """Pass-2 kernels to test on a case: one node per thread, and two per thread where nx is even."""
+    return [1, 2] if CASES[name][0]["shape"][0] % 2 == 0 else [1]
+
+
+@pytest.mark.parametrize("name,variant", [(n, v) for n in CASES for v in _variants(n)])
+def test_fp32_matches_oracle(cuda, name, variant):
     """FP32 arithmetic and storage.  Each stored population is rounded to 2^-24 relative every step;
     the 27 roundings that enter a node's momentum, accumulated as a random walk over 100 steps,
     give sqrt(100 * 27) * 2^-24 * max(rho) ~ 3e-6 max(rho) on u.  Densities: 2e-5 of max(rho)."""
     work, u_amp = CASES[name]
-    lat, orc = _pair(work, u_amp, "f32")
+    lat, orc = _pair(work, u_amp, "f32", variant=variant)
     lat.step(100)
     orc.step(100)
     gr, gb, gu = lat.macro()
@@ -65,14 +70,15 @@ def test_fp32_matches_oracle(cuda, name):
     lat.close()
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
-@pytest.mark.parametrize("name", ["static_droplet_32", "rayleigh_taylor_16", "jet_24x20x40"])
-def test_packed_storage_error_budget(cuda, name, storage):
+@pytest.mark.parametrize("name", ["static_droplet_32", "rayleigh_taylor_16", "jet_32x20x40"])
+def test_packed_storage_error_budget(cuda, name, storage, variant):
     """16-bit deviation + 16-bit red fraction storage, FP32 arithmetic.  The deviation carries
     2^-11 (half) or 2^-8 (bfloat16) relative error per store and the red fraction 2^-17 absolute;
     after 100 steps the densities stay within 2e-3 (half) / 1e-2 (bfloat16) of the oracle."""
     work, u_amp = CASES[name]
-    lat, orc = _pair(work, u_amp, storage)
+    lat, orc = _pair(work, u_amp, storage, variant=variant)
     lat.step(100)
     orc.step(100)
     gr, gb, gu = lat.macro()
@@ -85,8 +91,27 @@ def test_packed_storage_error_budget(cuda, name, storage):
     lat.close()
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_one_and_two_nodes_per_thread_agree(cuda, storage):
+    """The two pass-2 kernels compute the same update; they differ only in FP32 rounding order."""
+    work, u_amp = CASES["jet_32x20x40"]
+    rr, rb, u = L.initial_fields(work, seed=5, u_amp=0.01)
+    a = pkg.Lattice(work["shape"], work["params"], storage=storage, variant=1)
+    b = pkg.Lattice(work["shape"], work["params"], storage=storage, variant=2)
+    for lat in (a, b):
+        lat.init_fields(rr, rb, u)
+        lat.step(50)
+    ra, ba, ua = a.macro()
+    rb_, bb, ub = b.macro()
+    tol = 2e-5 if storage == "f32" else 2e-3
+    assert np.max(np.abs(ra - rb_)) < tol and np.max(np.abs(ba - bb)) < tol
+    assert np.max(np.abs(ua - ub)) < 50 * tol * np.max(np.abs(ua))
+    a.close()
+    b.close()
+
+
 def test_graph_replay_equals_direct_launches(cuda):
-    work, u_amp = CASES["jet_24x20x40"]
+    work, u_amp = CASES["jet_32x20x40"]
     rr, rb, u = L.initial_fields(work, seed=1, u_amp=u_amp)
     a = pkg.Lattice(work["shape"], work["params"], storage="f32")
     b = pkg.Lattice(work["shape"], work["params"], storage="f32")

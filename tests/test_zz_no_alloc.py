@@ -37,7 +37,7 @@ def _check_against_lbm_diag(lat, out):
 def test_static_diag_matches_lbm_diag_on_two_calls(cuda):
     import torch
 
-    w = L.jet(nx=24, ny=20, nz=40, D=8.0, Re=200.0, nu_c=2e-3, A=0.004)
+    w = L.jet(nx=32, ny=20, nz=40, D=8.0, Re=200.0, nu_c=2e-3, A=0.004)
     rr0, rb0, u0 = L.initial_fields(w)
     p = w["params"]
     lat = pkg.Lattice(w["shape"], p, storage="f64")
