@@ -221,6 +221,36 @@ LBM_EXPORT lbm_status lbm_moment_matrix(double* M);
  * Returns LBM_OK or LBM_EINVAL with a message in *msg (static storage). */
 LBM_EXPORT lbm_status lbm_selfcheck(const char** msg);
 
+/* Pick the faster collide-stream kernel for this handle by measurement: take
+ * `steps` steps (>= 1) with each available kernel (one node per thread; two
+ * nodes per thread where the storage and nx allow), timed with CUDA events on
+ * the handle's stream, keep the faster one for later steps and report it in
+ * *chosen (1 or 2; may be NULL).  The tuning steps are ordinary time steps:
+ * both kernels compute the same update, so the time advances by 2*steps (or
+ * by steps when only one kernel applies).  Synchronises. */
+LBM_EXPORT lbm_status lbm_autotune(lbm* h, int steps, int* chosen);
+
+/* Batched stepping of several independent boxes (e.g. the jets of a regime
+ * sweep): one CUDA graph holds, per handle, its own chain of kernels as an
+ * independent branch, so one graph launch advances every box and boxes of
+ * different sizes run concurrently.  The handles stay owned by the caller and
+ * must outlive the batch; they must all be at the same step parity (t mod 2)
+ * whenever lbm_batch_step is called (LBM_ESTATE otherwise).  Work goes on
+ * cuda_stream (NULL = legacy default stream), ordered after the work already
+ * queued on each handle's own stream, and each handle's stream is made to
+ * wait for it, so per-handle calls before and after a batch step stay in
+ * stream order.  The graph records each handle's kernel choice when first
+ * launched: autotune before stepping. */
+typedef struct lbm_batch lbm_batch;
+LBM_EXPORT lbm_status lbm_batch_create(lbm* const* handles, int n, void* cuda_stream, lbm_batch** out);
+/* Advance every handle by n >= 0 steps (graph launches of 16 steps, then
+ * single steps).  Asynchronous. */
+LBM_EXPORT lbm_status lbm_batch_step(lbm_batch* b, int n);
+/* Wait for the batch's stream; LBM_EUNSTABLE if any handle's watchdog fired. */
+LBM_EXPORT lbm_status lbm_batch_synchronize(lbm_batch* b);
+/* Release the batch (not the handles).  NULL is a no-op. */
+LBM_EXPORT void lbm_batch_free(lbm_batch* b);
+
 /* Allocation-free diagnostics; the paper has no counterpart (it is an
  * interface for callers, not part of the method).  Reduces caller-owned device
  * fields rhoR, rhoB (N = nx*ny*nz doubles each, x fastest, e.g. filled by

@@ -180,3 +180,57 @@ def parity_cases():
     j = jet(nx=32, ny=20, nz=40, D=8.0, Re=200.0, nu_c=2e-3, A=0.004)
     cases.append(("jet_32x20x40", j, 0.0))
     return cases
+
+
+# --------------------------------------------------------------------------
+# batched regime-map sweep (many independent jets)
+
+REGIMES = ("dripping", "varicose", "sinuous", "atomization")
+
+
+def regime_label(Re, Oh, We):
+    """Breakup regime on the Saito 2017 map quoted in Sec. IV.C: Oh = 2.8/Re separates varicose (I)
+    from sinuous (II) and Oh = 22/Re sinuous from atomization (III).  The dripping (0) boundary is
+    not given in the paper; jets with We < 4 are labelled dripping here (a stated reading)."""
+    if We < 4.0:
+        return 0
+    if Oh < 2.8 / Re:
+        return 1
+    if Oh < 22.0 / Re:
+        return 2
+    return 3
+
+
+def regime_sweep(n=64, seed=2024, steps=20000, eta=3.0, Fr=8.5, A_max=0.02, nu_max=0.015, u_max=0.1):
+    """`n` jets (configs of the batched sweep): grids nx = ny in {64, 80, 96} with nz = 4 nx, nozzle
+    D in 8..12, (Re, Oh) log-uniform over [10, 3e3] x [1e-3, 1], gamma uniform in [1.1, 1.5],
+    eta = 3, Fr = 8.5.  Lattice mapping: nu_j = min(u_max D/Re, nu_max) (nu_max keeps the MRT with
+    Suga's rates in its stable range), u_j0 = Re nu_j / D, nu_c = nu_j/eta, We = (Re Oh)^2,
+    sigma = rho_j u_j0^2 D / We, A = 9 sigma / (4 tau) with tau at the interface, capped at A_max
+    (the achieved Oh is recorded), g = u_j0^2/(Fr D)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        nxy = int(rng.choice([64, 80, 96]))
+        D = float(rng.integers(8, 13))
+        Re = float(10 ** rng.uniform(1.0, math.log10(3e3)))
+        Oh = float(10 ** rng.uniform(-3.0, 0.0))
+        gamma = float(rng.uniform(1.1, 1.5))
+        nu_j = min(u_max * D / Re, nu_max)
+        u = Re * nu_j / D
+        nu_c = nu_j / eta
+        We = (Re * Oh) ** 2
+        sigma = u * u * D / We
+        tau = 3.0 * 0.5 * (nu_j + nu_c) + 0.5
+        A = min(9.0 * sigma / (4.0 * tau), A_max)
+        sigma_eff = 4.0 / 9.0 * A * tau
+        We_eff = u * u * D / sigma_eff
+        Oh_eff = math.sqrt(We_eff) / Re
+        w = jet(nx=nxy, ny=nxy, nz=4 * nxy, D=D, Re=Re, nu_c=nu_c, gamma=gamma, eta=eta, A=A, Fr=Fr,
+                noise=0.01, seed=seed * 1000 + k)
+        w["name"] = f"sweep_{k:02d}_{nxy}x{nxy}x{4 * nxy}_D{D:g}"
+        w["steps"] = steps
+        w["groups"] = dict(Re=Re, Oh=Oh_eff, We=We_eff, gamma=gamma, eta=eta, Oh_target=Oh,
+                           regime=regime_label(Re, Oh_eff, We_eff), u_j0=u, D=D)
+        out.append(w)
+    return out

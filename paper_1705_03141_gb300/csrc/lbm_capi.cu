@@ -8,6 +8,7 @@
 
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/lbm.h"
 #include "lbm_dispatch.h"
@@ -615,12 +616,208 @@ lbm_status lbm_selfcheck(const char** msg) {
   return LBM_OK;
 }
 
+lbm_status lbm_autotune(lbm* h, int steps, int* chosen) {
+  if (!h) return LBM_EINVAL;
+  if (steps < 1) return fail(h, LBM_EINVAL, "steps must be >= 1");
+  const bool two = h->ks->has_paired && h->nx % 2 == 0;
+  if (!two) {
+    h->variant = 1;
+    lbm_status st = lbm_step(h, steps);
+    if (st != LBM_OK) return st;
+    if (chosen) *chosen = 1;
+    return lbm_synchronize(h);
+  }
+  float ms[2] = {0.f, 0.f};
+  cudaEvent_t e0, e1;
+  LBM_CUDA(h, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(h, LBM_ECUDA, "cudaEventCreate failed");
+  }
+  lbm_status st = LBM_OK;
+  for (int v = 1; v <= 2 && st == LBM_OK; ++v) {
+    h->variant = v;
+    // direct launches: both kernels timed the same way, no graph capture in between
+    if (cudaEventRecord(e0, h->stream) != cudaSuccess) st = fail(h, LBM_ECUDA, "cudaEventRecord failed");
+    for (int k = 0; k < steps && st == LBM_OK; ++k) {
+      st = enqueue_step(h, h->t, h->stream);
+      if (st == LBM_OK) h->t += 1;
+    }
+    if (st == LBM_OK && (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                         cudaEventElapsedTime(&ms[v - 1], e0, e1) != cudaSuccess))
+      st = fail(h, LBM_ECUDA, "autotune timing: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != LBM_OK) return st;
+  h->variant = ms[1] < ms[0] ? 2 : 1;
+  drop_graphs(h);  // captured graphs hold the kernel of the previous choice
+  if (chosen) *chosen = h->variant;
+  return check_flag(h);
+}
+
 void lbm_free(lbm* h) {
   if (!h) return;
   drop_graphs(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->own_ws && h->ws) cudaFree(h->ws);
   delete h;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batches: one graph with an independent branch per handle
+
+struct lbm_batch {
+  std::vector<lbm*> h;
+  cudaStream_t stream;
+  cudaStream_t root;                 // capture root
+  std::vector<cudaStream_t> branch;  // one capture stream per handle
+  cudaGraphExec_t graph[2];          // kGraphSteps steps from an even / odd parity
+  std::vector<cudaEvent_t> ready;    // per handle: its own stream's work so far
+  cudaEvent_t done;                  // the batch stream's work so far
+  std::string err;
+};
+
+namespace {
+
+void batch_drop(lbm_batch* b) {
+  for (int k = 0; k < 2; ++k)
+    if (b->graph[k]) {
+      cudaGraphExecDestroy(b->graph[k]);
+      b->graph[k] = nullptr;
+    }
+}
+
+lbm_status batch_build(lbm_batch* b, int parity) {
+  cudaGraph_t g = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins(b->h.size(), nullptr);
+  lbm_status st = LBM_OK;
+  if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
+  for (auto& e : joins)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) st = LBM_ECUDA;
+  if (st == LBM_OK && cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = LBM_ECUDA;
+  if (st == LBM_OK) {
+    cudaEventRecord(fork, b->root);
+    for (size_t i = 0; i < b->h.size() && st == LBM_OK; ++i) {
+      cudaStreamWaitEvent(b->branch[i], fork, 0);
+      for (int k = 0; k < kGraphSteps && st == LBM_OK; ++k) st = enqueue_step(b->h[i], parity + k, b->branch[i]);
+      cudaEventRecord(joins[i], b->branch[i]);
+      cudaStreamWaitEvent(b->root, joins[i], 0);
+    }
+    cudaError_t e = cudaStreamEndCapture(b->root, &g);
+    if (st == LBM_OK && e != cudaSuccess) st = LBM_ECUDA;
+  }
+  if (st == LBM_OK && cudaGraphInstantiate(&b->graph[parity], g, 0) != cudaSuccess) {
+    b->graph[parity] = nullptr;
+    st = LBM_ECUDA;
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaEventDestroy(fork);
+  for (auto& e : joins)
+    if (e) cudaEventDestroy(e);
+  if (st != LBM_OK) {
+    cudaGetLastError();
+    b->err = "batch graph capture failed";
+  }
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_create(lbm* const* handles, int n, void* cuda_stream, lbm_batch** out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  if (!handles || n < 1) return LBM_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!handles[i]) return LBM_EINVAL;
+  lbm_batch* b = new (std::nothrow) lbm_batch();
+  if (!b) return LBM_ENOMEM;
+  b->h.assign(handles, handles + n);
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->graph[0] = b->graph[1] = nullptr;
+  b->root = nullptr;
+  bool ok = cudaStreamCreateWithFlags(&b->root, cudaStreamNonBlocking) == cudaSuccess;
+  b->done = nullptr;
+  b->branch.assign(n, nullptr);
+  b->ready.assign(n, nullptr);
+  for (int i = 0; i < n && ok; ++i) ok = cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking) == cudaSuccess;
+  for (int i = 0; i < n && ok; ++i) ok = cudaEventCreateWithFlags(&b->ready[i], cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    lbm_batch_free(b);
+    return LBM_ECUDA;
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int n) {
+  if (!b || n < 0) return LBM_EINVAL;
+  const long long t0 = b->h[0]->t;
+  for (lbm* h : b->h) {
+    if (((h->t - t0) & 1) != 0) return LBM_ESTATE;
+    if (h->unstable) return LBM_EUNSTABLE;
+  }
+  // the batch stream first waits for whatever each handle's own stream has queued ...
+  for (size_t i = 0; i < b->h.size(); ++i) {
+    if (b->h[i]->stream == b->stream) continue;
+    if (cudaEventRecord(b->ready[i], b->h[i]->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(b->stream, b->ready[i], 0) != cudaSuccess)
+      return LBM_ECUDA;
+  }
+  int k = 0;
+  if (n >= kGraphSteps) {
+    const int parity = (int)(t0 & 1);
+    if (!b->graph[parity]) {
+      lbm_status st = batch_build(b, parity);
+      if (st != LBM_OK) return st;
+    }
+    for (; k + kGraphSteps <= n; k += kGraphSteps) {
+      if (cudaGraphLaunch(b->graph[parity], b->stream) != cudaSuccess) return LBM_ECUDA;
+      for (lbm* h : b->h) h->t += kGraphSteps;
+    }
+  }
+  // the graph runs on the batch stream; later single steps of each handle go on that stream too
+  for (; k < n; ++k)
+    for (lbm* h : b->h) {
+      lbm_status st = enqueue_step(h, h->t, b->stream);
+      if (st != LBM_OK) return st;
+      h->t += 1;
+    }
+  // ... and each handle's stream then waits for the batch, so later per-handle calls stay in order
+  if (cudaEventRecord(b->done, b->stream) != cudaSuccess) return LBM_ECUDA;
+  for (lbm* h : b->h)
+    if (h->stream != b->stream && cudaStreamWaitEvent(h->stream, b->done, 0) != cudaSuccess) return LBM_ECUDA;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_synchronize(lbm_batch* b) {
+  if (!b) return LBM_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LBM_ECUDA;
+  lbm_status worst = LBM_OK;
+  for (lbm* h : b->h) {
+    lbm_status st = lbm_synchronize(h);
+    if (st != LBM_OK) worst = st;
+  }
+  return worst;
+}
+
+void lbm_batch_free(lbm_batch* b) {
+  if (!b) return;
+  batch_drop(b);
+  for (auto s : b->branch)
+    if (s) cudaStreamDestroy(s);
+  for (auto e : b->ready)
+    if (e) cudaEventDestroy(e);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->root) cudaStreamDestroy(b->root);
+  delete b;
 }
 
 }  // extern "C"

@@ -26,7 +26,8 @@ Q = 27
 SYMBOLS = ["lbm_workspace_size", "lbm_create", "lbm_init_fields", "lbm_set_inflow", "lbm_step", "lbm_macro",
            "lbm_diag", "lbm_get_populations", "lbm_set_populations", "lbm_profile_step", "lbm_set_stream", "lbm_synchronize", "lbm_time",
            "lbm_kernels_per_step", "lbm_last_error", "lbm_status_string", "lbm_moment_matrix", "lbm_selfcheck",
-           "lbm_diag_fields_static", "lbm_free"]
+           "lbm_diag_fields_static", "lbm_autotune", "lbm_batch_create", "lbm_batch_step", "lbm_batch_synchronize",
+           "lbm_batch_free", "lbm_free"]
 
 
 class LbmError(RuntimeError):
@@ -87,6 +88,12 @@ def library():
         lib.lbm_moment_matrix.argtypes = [vp]
         lib.lbm_selfcheck.argtypes = [P(ctypes.c_char_p)]
         lib.lbm_diag_fields_static.argtypes = [vp, vp, i, i, i, d, d, vp, vp, P(ctypes.c_char_p)]
+        lib.lbm_autotune.argtypes = [h, i, P(i)]
+        lib.lbm_batch_create.argtypes = [P(h), i, vp, P(h)]
+        lib.lbm_batch_step.argtypes = [h, i]
+        lib.lbm_batch_synchronize.argtypes = [h]
+        lib.lbm_batch_free.argtypes = [h]
+        lib.lbm_batch_free.restype = None
         lib.lbm_free.argtypes = [h]
         lib.lbm_free.restype = None
         for name in SYMBOLS:
@@ -262,6 +269,12 @@ class Lattice:
     def synchronize(self):
         _check(library().lbm_synchronize(self._h), self._h)
 
+    def autotune(self, steps=8):
+        """Time both collide-stream kernels on `steps` real steps each; keep the faster (returns 1 or 2)."""
+        c = ctypes.c_int()
+        _check(library().lbm_autotune(self._h, int(steps), ctypes.byref(c)), self._h)
+        return c.value
+
     def macro(self, out=None):
         """(rho_r, rho_b, u) as (nz, ny, nx) / (3, nz, ny, nx) float64 arrays (host numpy, or the given buffers)."""
         sh = (self.nz, self.ny, self.nx)
@@ -289,6 +302,43 @@ class Lattice:
     def set_populations(self, f, t=0):
         ff = _as_f64(f)
         _check(library().lbm_set_populations(self._h, _ptr(ff), int(t)), self._h)
+
+
+class Batch:
+    """Several Lattices advanced together by one CUDA graph (one independent branch per lattice)."""
+
+    def __init__(self, lattices, stream=None):
+        import torch
+
+        self.lattices = list(lattices)
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        arr = (ctypes.c_void_p * len(self.lattices))(*[lat._h for lat in self.lattices])
+        h = ctypes.c_void_p()
+        rc = library().lbm_batch_create(arr, len(self.lattices), self.stream.cuda_stream, ctypes.byref(h))
+        if rc != 0:
+            raise LbmError(rc, "lbm_batch_create failed")
+        self._h = h
+
+    def step(self, n=1):
+        rc = library().lbm_batch_step(self._h, int(n))
+        if rc != 0:
+            raise LbmError(rc, "lbm_batch_step failed")
+
+    def synchronize(self):
+        rc = library().lbm_batch_synchronize(self._h)
+        if rc != 0:
+            raise LbmError(rc, "lbm_batch_synchronize failed")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            library().lbm_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _as_f64(a):
