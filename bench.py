@@ -62,27 +62,46 @@ def peaks():
     return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ("lbm_f2.cuh", "lbm_kernels.cuh", "lbm_kernels_f16.cu", "lbm_kernels_f32.cu", "lbm_kernels_f64.cu",
+                  "lbm_lattice.cuh", "lbm_launch.cuh")
+
+
 def kernel_hash():
+    """Hash of the device-code sources of the stepping kernels (not of the host-side ABI)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1705_03141_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(storage):
-    """DRAM bytes per launch of the collide-stream kernel from the committed ncu summary, if it
-    was taken on the current kernel sources (else None)."""
+def profiled(storage, key):
+    """A figure of the collide-stream kernel from its committed ncu summary (`key: value` line),
+    if the summary was taken on the current kernel sources (else None)."""
     p = os.path.join(ROOT, "profiles", f"collide_stream_jet_{storage}.md")
     if not os.path.exists(p):
         return None
     txt = open(p).read()
     m = re.search(r"kernel_sources_sha:\s*([0-9a-f]+)", txt)
-    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    t = re.search(key + r":\s*([0-9.eE+]+)", txt)
     if not m or not t or m.group(1) != kernel_hash():
         return None
     return float(t.group(1))
+
+
+def profiled_traffic(storage):
+    """DRAM bytes per launch of the collide-stream kernel (ncu, current sources) or None."""
+    return profiled(storage, "dram_bytes_per_launch")
+
+
+def alu_roof(pkg, storage, nodes, launch_ms, fp32_peak):
+    """FP32 roof of the collide-stream kernel: FLOP per node counted by ncu (fadd + fmul + 2 ffma
+    thread instructions), over the event-timed launch, against the measured CUDA-core peak."""
+    flop = profiled(storage, "fp32_flop_per_node")
+    achieved = flop * nodes / (launch_ms * 1e-3) / 1e12 if flop else None
+    return {"bound": "alu", "flop_per_node": flop, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak if achieved and fp32_peak else None,
+            "peak_kind": "measured (lbm_measure_fp32_peak: best of FFMA and FFMA2 chains)"}
 
 
 class ClockSampler:
@@ -367,11 +386,16 @@ def main():
     alg_bytes = N * (POP_BYTES[args.storage] * 2 + DENS_BYTES[args.storage])
     achieved = alg_bytes / (ms[1] * 1e-3) / 1e9
     traffic = profiled_traffic(args.storage)
+    fp32_peak = max(pkg.measure_fp32_peak(False), pkg.measure_fp32_peak(True))
     roof = {"bound": "hbm", "kernel": "k_collide_stream", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
             "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": ms[1],
             "density_pass_ms": ms[0], "outflow_ms": ms[2],
-            "step_share_collide": ms[1] / max(sum(ms), 1e-12)}
+            "step_share_collide": ms[1] / max(sum(ms), 1e-12),
+            "alu": alu_roof(pkg, args.storage, N, ms[1], fp32_peak)}
+    if fp32 is not None:
+        fp32["collide_alu"] = alu_roof(pkg, "f32", N, fp32["collide_ms"], fp32_peak)
+        fp32["collide_hbm_frac"] = fp32["collide_gbs"] / peak
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

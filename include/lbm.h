@@ -251,6 +251,15 @@ LBM_EXPORT lbm_status lbm_batch_synchronize(lbm_batch* b);
 /* Release the batch (not the handles).  NULL is a no-op. */
 LBM_EXPORT void lbm_batch_free(lbm_batch* b);
 
+/* Measured FP32 CUDA-core throughput of the current device (a measurement
+ * utility; the paper has no counterpart): the ALU roof of the stepping
+ * kernels, whose arithmetic is FP32 FMA/ADD/MUL.  Runs 8 independent FMA
+ * chains per thread on 8 blocks of 256 threads per SM (packed != 0: the same
+ * FLOPs as packed FP32x2 FMAs), best of three timed launches on cuda_stream
+ * (NULL = legacy default stream), and writes TFLOP/s (2 per FMA) to *tflops.
+ * Allocates and frees a small device buffer; synchronises. */
+LBM_EXPORT lbm_status lbm_measure_fp32_peak(void* cuda_stream, int packed, double* tflops);
+
 /* Allocation-free diagnostics; the paper has no counterpart (it is an
  * interface for callers, not part of the method).  Reduces caller-owned device
  * fields rhoR, rhoB (N = nx*ny*nz doubles each, x fastest, e.g. filled by

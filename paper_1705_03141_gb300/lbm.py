@@ -27,7 +27,7 @@ SYMBOLS = ["lbm_workspace_size", "lbm_create", "lbm_init_fields", "lbm_set_inflo
            "lbm_diag", "lbm_get_populations", "lbm_set_populations", "lbm_profile_step", "lbm_set_stream", "lbm_synchronize", "lbm_time",
            "lbm_kernels_per_step", "lbm_last_error", "lbm_status_string", "lbm_moment_matrix", "lbm_selfcheck",
            "lbm_diag_fields_static", "lbm_autotune", "lbm_batch_create", "lbm_batch_step", "lbm_batch_synchronize",
-           "lbm_batch_free", "lbm_free"]
+           "lbm_batch_free", "lbm_measure_fp32_peak", "lbm_free"]
 
 
 class LbmError(RuntimeError):
@@ -94,6 +94,7 @@ def library():
         lib.lbm_batch_synchronize.argtypes = [h]
         lib.lbm_batch_free.argtypes = [h]
         lib.lbm_batch_free.restype = None
+        lib.lbm_measure_fp32_peak.argtypes = [vp, i, P(d)]
         lib.lbm_free.argtypes = [h]
         lib.lbm_free.restype = None
         for name in SYMBOLS:
@@ -138,6 +139,16 @@ def selfcheck() -> str:
     if rc != 0:
         raise LbmError(rc, msg.value.decode())
     return msg.value.decode()
+
+
+def measure_fp32_peak(packed=False, stream=None):
+    """Measured FP32 CUDA-core TFLOP/s of the current device (FMA = 2 FLOP)."""
+    import torch
+
+    st = torch.cuda.current_stream() if stream is None else stream
+    v = ctypes.c_double()
+    _check(library().lbm_measure_fp32_peak(st.cuda_stream, int(bool(packed)), ctypes.byref(v)), None)
+    return v.value
 
 
 def diag_fields_static(rho_r, rho_b, rho_r0, rho_b0, out=None, stream=None):
