@@ -75,10 +75,21 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def profiled(storage, key):
+def profile_name(storage, variant):
+    return f"collide_stream{'_fused' if variant == 3 else ''}_jet_{storage}.md"
+
+
+def collide_bytes(storage, variant):
+    """Algorithmic bytes per node of one collide-stream launch: every population read and written
+    once, plus (rho, phi) of pass 1 (two-pass) or the fixed-point (rho, rho_r) read and the next
+    step's written once (fused density pass, 2 x 8 bytes)."""
+    return POP_BYTES[storage] * 2 + (16 if variant == 3 else DENS_BYTES[storage])
+
+
+def profiled(storage, key, variant=1):
     """A figure of the collide-stream kernel from its committed ncu summary (`key: value` line),
     if the summary was taken on the current kernel sources (else None)."""
-    p = os.path.join(ROOT, "profiles", f"collide_stream_jet_{storage}.md")
+    p = os.path.join(ROOT, "profiles", profile_name(storage, variant))
     if not os.path.exists(p):
         return None
     txt = open(p).read()
@@ -89,15 +100,15 @@ def profiled(storage, key):
     return float(t.group(1))
 
 
-def profiled_traffic(storage):
+def profiled_traffic(storage, variant=1):
     """DRAM bytes per launch of the collide-stream kernel (ncu, current sources) or None."""
-    return profiled(storage, "dram_bytes_per_launch")
+    return profiled(storage, "dram_bytes_per_launch", variant)
 
 
-def alu_roof(pkg, storage, nodes, launch_ms, fp32_peak):
+def alu_roof(pkg, storage, nodes, launch_ms, fp32_peak, variant=1):
     """FP32 roof of the collide-stream kernel: FLOP per node counted by ncu (fadd + fmul + 2 ffma
     thread instructions), over the event-timed launch, against the measured CUDA-core peak."""
-    flop = profiled(storage, "fp32_flop_per_node")
+    flop = profiled(storage, "fp32_flop_per_node", variant)
     achieved = flop * nodes / (launch_ms * 1e-3) / 1e12 if flop else None
     return {"bound": "alu", "flop_per_node": flop, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak if achieved and fp32_peak else None,
@@ -299,7 +310,7 @@ def main():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variant", type=int, default=0, help="collide-stream kernel: 0 library choice, 1 one node "
-                    "per thread, 2 two nodes per thread")
+                    "per thread, 2 two nodes per thread, 3 fused density pass")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -353,6 +364,7 @@ def main():
     dt_max = max_over_ranks(dt, ws, dev)
     mlups = ws * N * args.steps / dt_max / 1e6
     kps = lat.kernels_per_step
+    variant = lat.variant
     diag_h = lat.diag()
     # live per-kernel timing of the same configuration (CUDA events on the kernels' stream)
     ms = lat.profile_step(min(200, args.steps))
@@ -364,13 +376,16 @@ def main():
         lat32 = make("f32")
         lat32.step(args.warmup)
         dt32 = max_over_ranks(timed(lat32, args.steps), ws, dev)
+        variant32 = lat32.variant
         diag32 = lat32.diag()
         ms32 = lat32.profile_step(min(200, args.steps))
         lat32.close()
         D = w["params"]["inflow"]["D"]
-        bytes32 = N * (POP_BYTES["f32"] * 2 + DENS_BYTES["f32"])
+        bytes32 = N * collide_bytes("f32", variant32)
         fp32 = {"value": ws * N * args.steps / dt32 / 1e6, "ms_per_step": dt32 / args.steps * 1e3,
-                "collide_ms": ms32[1], "collide_gbs": bytes32 / (ms32[1] * 1e-3) / 1e9,
+                "variant": variant32, "pass1_ms": ms32[0], "collide_ms": ms32[1],
+                "collide_gbs": bytes32 / (ms32[1] * 1e-3) / 1e9, "collide_bytes_per_node": bytes32 // N,
+                "collide_traffic": profiled_traffic("f32", variant32),
                 "stated_error": {
                     "after_steps": args.warmup + args.steps,
                     "leading_edge_abs_diff_over_D": abs(diag_h["z_le"] - diag32["z_le"]) / D,
@@ -383,18 +398,18 @@ def main():
 
     # ---- roofline of the dominant kernel ----------------------------------
     peak, peak_kind = peaks()
-    alg_bytes = N * (POP_BYTES[args.storage] * 2 + DENS_BYTES[args.storage])
+    alg_bytes = N * collide_bytes(args.storage, variant)
     achieved = alg_bytes / (ms[1] * 1e-3) / 1e9
-    traffic = profiled_traffic(args.storage)
+    traffic = profiled_traffic(args.storage, variant)
     fp32_peak = max(pkg.measure_fp32_peak(False), pkg.measure_fp32_peak(True))
     roof = {"bound": "hbm", "kernel": "k_collide_stream", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
             "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": ms[1],
-            "density_pass_ms": ms[0], "outflow_ms": ms[2],
+            "variant": variant, "density_pass_ms": ms[0], "outflow_ms": ms[2],
             "step_share_collide": ms[1] / max(sum(ms), 1e-12),
-            "alu": alu_roof(pkg, args.storage, N, ms[1], fp32_peak)}
+            "alu": alu_roof(pkg, args.storage, N, ms[1], fp32_peak, variant)}
     if fp32 is not None:
-        fp32["collide_alu"] = alu_roof(pkg, "f32", N, fp32["collide_ms"], fp32_peak)
+        fp32["collide_alu"] = alu_roof(pkg, "f32", N, fp32["collide_ms"], fp32_peak, fp32["variant"])
         fp32["collide_hbm_frac"] = fp32["collide_gbs"] / peak
 
     cpu = None

@@ -125,10 +125,18 @@ typedef struct {
                             aligned and outlive the handle.  NULL: the library
                             allocates (cudaMalloc) and frees it itself. */
   size_t workspace_bytes;
-  int variant;           /* collide-stream kernel: 0 = library's choice (currently 1),
+  int variant;           /* collide-stream kernel: 0 = library's choice (3 for F32
+                            storage, 1 otherwise: the measured faster one),
                             1 = one node per thread, 2 = two x-adjacent nodes per
                             thread with packed FP32x2 arithmetic (needs F32/F16/BF16
-                            storage and an even nx) */
+                            storage and an even nx), 3 = one node per thread with
+                            the fused density pass: the collide-stream kernel also
+                            accumulates the next step's densities, so the separate
+                            density pass is skipped (needs F32/F16/BF16 storage).
+                            Variants 1 and 2 compute identical results; variant 3
+                            differs from them only by the rounding of the densities
+                            that enter the gradients, and is bitwise reproducible.
+                            F32/F16/BF16 storage needs rho_r0, rho_b0 <= 64. */
 } lbm_params;
 
 typedef struct lbm lbm; /* opaque handle; owns all device state it allocated */
@@ -202,8 +210,13 @@ LBM_EXPORT lbm_status lbm_synchronize(lbm* h);
 /* Current time step index t (number of steps taken since initialisation). */
 LBM_EXPORT long long lbm_time(const lbm* h);
 
-/* Number of kernel launches one lbm_step(h, 1) enqueues. */
+/* Number of kernel launches one lbm_step(h, 1) enqueues (the fused density
+ * pass also enqueues one memset per step, not counted). */
 LBM_EXPORT int lbm_kernels_per_step(const lbm* h);
+
+/* The collide-stream kernel variant the handle runs (1, 2 or 3; see
+ * lbm_params.variant and lbm_autotune); -1 for NULL. */
+LBM_EXPORT int lbm_kernel_variant(const lbm* h);
 
 /* Last error message of this handle ("" if none); valid until the next call. */
 LBM_EXPORT const char* lbm_last_error(const lbm* h);
@@ -221,13 +234,13 @@ LBM_EXPORT lbm_status lbm_moment_matrix(double* M);
  * Returns LBM_OK or LBM_EINVAL with a message in *msg (static storage). */
 LBM_EXPORT lbm_status lbm_selfcheck(const char** msg);
 
-/* Pick the faster collide-stream kernel for this handle by measurement: take
- * `steps` steps (>= 1) with each available kernel (one node per thread; two
- * nodes per thread where the storage and nx allow), timed with CUDA events on
- * the handle's stream, keep the faster one for later steps and report it in
- * *chosen (1 or 2; may be NULL).  The tuning steps are ordinary time steps:
- * both kernels compute the same update, so the time advances by 2*steps (or
- * by steps when only one kernel applies).  Synchronises. */
+/* Pick the fastest collide-stream kernel for this handle by measurement: take
+ * `steps` steps (>= 1) with each available variant (1; 2 where the storage and
+ * nx allow; 3 for F32/F16/BF16 storage), timed with CUDA events on the
+ * handle's stream, keep the fastest for later steps and report it in *chosen
+ * (1, 2 or 3; may be NULL).  The tuning steps are ordinary time steps of the
+ * same update, so the time advances by steps times the number of variants
+ * tried (1 for F64 storage, 2 or 3 otherwise).  Synchronises. */
 LBM_EXPORT lbm_status lbm_autotune(lbm* h, int steps, int* chosen);
 
 /* Batched stepping of several independent boxes (e.g. the jets of a regime

@@ -25,7 +25,7 @@ constexpr int kGraphSteps = 16;  // steps per captured CUDA graph
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {  // byte offsets inside the device workspace
-  size_t pop, dens, top, counter, flag, partial, diag_out, scratch, total;
+  size_t pop, dens, fix, top, counter, flag, partial, diag_out, scratch, total;
 };
 
 }  // namespace
@@ -41,11 +41,13 @@ struct lbm {
   char* ws;
   bool own_ws;
   void *pop, *dens, *top, *partial;
-  long long* counter;
+  int* fix[2];      // fused density pass: [rho | rho_r] fixed-point accumulators of the state at an even / odd step
+  bool fix_ready;   // fix[t & 1] holds the densities of the current state
+  long long* counter;  // [2]: step index, see k_collide_stream
   int* flag;
   double *diag_out, *scratch;
   int diag_blocks;
-  int variant;  // pass-2 kernel: 1 = one node per thread, 2 = two nodes per thread
+  int variant;  // pass-2 kernel: 1 = one node per thread, 2 = two nodes per thread, 3 = fused density
   cudaStream_t stream;
   cudaStream_t cap_stream;
   cudaGraphExec_t graph[2];  // kGraphSteps steps starting at an even / odd step
@@ -111,9 +113,13 @@ const char* validate(int nx, int ny, int nz, const lbm_params* p) {
     if (p->bc[f] == LBM_BC_OUTFLOW && f != 5) return "OUTFLOW is only allowed on the +z face";
   }
   if (p->storage < 0 || p->storage > 3) return "unknown storage";
-  if (p->variant < 0 || p->variant > 2) return "unknown kernel variant";
+  if (p->variant < 0 || p->variant > 3) return "unknown kernel variant";
   if (p->variant == 2 && (p->storage == LBM_STORE_F64 || nx % 2 != 0))
     return "the two-nodes-per-thread kernel needs FP32 arithmetic (not F64 storage) and an even nx";
+  if (p->variant == 3 && p->storage == LBM_STORE_F64)
+    return "the fused density pass needs FP32 arithmetic (not F64 storage)";
+  if (p->storage != LBM_STORE_F64 && (p->rho_r0 > 64.0 || p->rho_b0 > 64.0))
+    return "FP32 storages need rho_r0, rho_b0 <= 64 (fixed-point range of the fused density pass)";
   return nullptr;
 }
 
@@ -129,10 +135,12 @@ Layout plan(int nx, int ny, int nz, const lbm_params* p, const KernelSet* ks, in
   o = align_up(o + (size_t)ks->pop_planes * 27 * Ns * ks->pop_elem_bytes, 256);
   L.dens = o;
   o = align_up(o + (size_t)N * ks->dens_bytes, 256);
+  L.fix = o;
+  if (ks->has_fused) o = align_up(o + (size_t)4 * N * sizeof(int), 256);
   L.top = o;
   if (p->bc[5] == LBM_BC_OUTFLOW) o = align_up(o + (size_t)2 * 27 * Pn * ks->real_bytes, 256);
   L.counter = o;
-  o = align_up(o + sizeof(long long), 256);
+  o = align_up(o + 2 * sizeof(long long), 256);
   L.flag = o;
   o = align_up(o + sizeof(int), 256);
   L.partial = o;
@@ -170,12 +178,40 @@ void drop_graphs(lbm* h) {
     }
 }
 
-// enqueue one time step (the step with index h->t) on stream s
+// enqueue one time step (the step with index t) on stream s
 lbm_status enqueue_step(lbm* h, long long t, cudaStream_t s) {
   const int layout = (int)(t & 1);
-  LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, h->counter, s));
-  LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->variant, s));
-  if (h->p.bc[5] == LBM_BC_OUTFLOW) LBM_CUDA(h, h->ks->outflow(h->pop, h->G, h->P, (int)((t + 1) & 1), h->top, s));
+  const bool outflow = h->p.bc[5] == LBM_BC_OUTFLOW;
+  if (h->variant == 3) {
+    // fused density pass: no pass 1; the accumulators of t+1 start from zero
+    int *cur = h->fix[layout], *nxt = h->fix[layout ^ 1];
+    LBM_CUDA(h, cudaMemsetAsync(nxt, 0, sizeof(int) * 2 * (size_t)h->N, s));
+    LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, 3, cur, cur + h->N, nxt,
+                               nxt + h->N, h->flag, s));
+    if (outflow)
+      LBM_CUDA(h, h->ks->outflow(h->pop, h->G, h->P, layout ^ 1, h->top, nxt, nxt + h->N, s));
+    return LBM_OK;
+  }
+  h->fix_ready = false;  // steps without the fused pass leave its accumulators behind
+  LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, nullptr, nullptr, s));
+  LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->variant, nullptr, nullptr, nullptr,
+                             nullptr, h->flag, s));
+  if (outflow) LBM_CUDA(h, h->ks->outflow(h->pop, h->G, h->P, layout ^ 1, h->top, nullptr, nullptr, s));
+  return LBM_OK;
+}
+
+// before fused steps from a state the fused pass did not produce: fill the accumulators of step t
+lbm_status ensure_fix(lbm* h, cudaStream_t s) {
+  if (h->variant != 3 || h->fix_ready) return LBM_OK;
+  int* cur = h->fix[h->t & 1];
+  LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, (int)(h->t & 1), h->dens, h->flag, cur, cur + h->N, s));
+  h->fix_ready = true;
+  return LBM_OK;
+}
+
+// the step index of step t for k_collide_stream
+lbm_status set_counter(lbm* h, long long t) {
+  LBM_CUDA(h, cudaMemcpyAsync(h->counter + (t & 1), &t, sizeof t, cudaMemcpyHostToDevice, h->stream));
   return LBM_OK;
 }
 
@@ -246,9 +282,14 @@ lbm_status lbm_create(int nx, int ny, int nz, const lbm_params* p, lbm** out) {
   int64_t Ns = 0;
   h->L = plan(nx, ny, nz, p, h->ks, &Ns, &h->diag_blocks);
   h->stream = static_cast<cudaStream_t>(p->cuda_stream);
-  // default: one node per thread (on GB300 it keeps 24 warps per SM resident; the
-  // two-node kernel's register footprint leaves 8 and measured slower)
-  h->variant = p->variant != 0 ? p->variant : 1;
+  // default, as measured on GB300: FP32 storage runs the fused density pass (its
+  // collide-stream kernel is bandwidth-bound, so dropping the separate density pass
+  // pays); the packed storages and FP64 run one node per thread with the two-pass
+  // scheme (the packed kernel is issue-bound, and the fused accumulation costs more
+  // instructions than the density pass); the two-node kernel's register footprint
+  // leaves 8 warps per SM and measured slower everywhere
+  h->variant = p->variant != 0 ? p->variant : (p->storage == LBM_STORE_F32 ? 3 : 1);
+  h->fix_ready = false;
 
   Geom& G = h->G;
   G.nx = nx;
@@ -299,6 +340,8 @@ lbm_status lbm_create(int nx, int ny, int nz, const lbm_params* p, lbm** out) {
   }
   h->pop = h->ws + h->L.pop;
   h->dens = h->ws + h->L.dens;
+  h->fix[0] = reinterpret_cast<int*>(h->ws + h->L.fix);
+  h->fix[1] = h->fix[0] + 2 * h->N;
   h->top = h->ws + h->L.top;
   h->counter = reinterpret_cast<long long*>(h->ws + h->L.counter);
   h->flag = reinterpret_cast<int*>(h->ws + h->L.flag);
@@ -353,8 +396,11 @@ lbm_status lbm_init_fields(lbm* h, const double* rhoR, const double* rhoB, const
   }
   LBM_CUDA(h, h->ks->init(h->pop, h->G, h->P, dr, db, du, h->stream));
   h->t = 0;
-  const long long c0 = -1;
-  LBM_CUDA(h, cudaMemcpyAsync(h->counter, &c0, sizeof c0, cudaMemcpyHostToDevice, h->stream));
+  h->fix_ready = false;
+  {
+    lbm_status st = set_counter(h, 0);
+    if (st != LBM_OK) return st;
+  }
   LBM_CUDA(h, cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
   if (h->p.bc[5] == LBM_BC_OUTFLOW) LBM_CUDA(h, h->ks->top_from_state(h->pop, h->G, h->P, 0, h->top, h->stream));
   LBM_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -382,6 +428,10 @@ lbm_status lbm_step(lbm* h, int n) {
   if (!h || n < 0) return h ? fail(h, LBM_EINVAL, "n must be >= 0") : LBM_EINVAL;
   if (h->unstable) return fail(h, LBM_EUNSTABLE, "watchdog: non-finite or non-positive density seen");
   static const bool no_graphs = getenv("LBM_NO_GRAPHS") != nullptr;
+  {
+    lbm_status st = ensure_fix(h, h->stream);
+    if (st != LBM_OK) return st;
+  }
   int k = 0;
   if (!no_graphs && n >= kGraphSteps) {
     const int parity = (int)(h->t & 1);
@@ -479,8 +529,11 @@ lbm_status lbm_set_populations(lbm* h, const double* f, long long t) {
     LBM_CUDA(h, h->ks->set_pop(h->pop, h->G, h->P, layout, i, inr, inb, h->stream));
   }
   h->t = t;
-  const long long c0 = t - 1;
-  LBM_CUDA(h, cudaMemcpyAsync(h->counter, &c0, sizeof c0, cudaMemcpyHostToDevice, h->stream));
+  h->fix_ready = false;
+  {
+    lbm_status st = set_counter(h, t);
+    if (st != LBM_OK) return st;
+  }
   LBM_CUDA(h, cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
   if (h->p.bc[5] == LBM_BC_OUTFLOW) LBM_CUDA(h, h->ks->top_from_state(h->pop, h->G, h->P, layout, h->top, h->stream));
   LBM_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -503,16 +556,29 @@ lbm_status lbm_profile_step(lbm* h, int n, double* ms_out) {
       st = fail(h, LBM_ECUDA, "cudaEventCreate failed");
       break;
     }
+  if (st == LBM_OK) st = ensure_fix(h, h->stream);
+  const bool fused = h->variant == 3;
+  if (!fused) h->fix_ready = false;
   for (int k = 0; st == LBM_OK && k < n; ++k) {
     const long long t = h->t;
     const int layout = (int)(t & 1);
     cudaEvent_t* e = ev + per * k;
+    // the same launches as enqueue_step, with an event between them; with the fused density
+    // pass the first interval is the clearing of the next step's accumulators
+    int* cur = h->fix[layout];
+    int* nxt = h->fix[layout ^ 1];
+    const size_t nfix = sizeof(int) * 2 * (size_t)h->N;
     if (cudaEventRecord(e[0], h->stream) != cudaSuccess ||
-        h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, h->counter, h->stream) != cudaSuccess ||
+        (fused ? cudaMemsetAsync(nxt, 0, nfix, h->stream)
+               : h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, nullptr, nullptr, h->stream)) !=
+            cudaSuccess ||
         cudaEventRecord(e[1], h->stream) != cudaSuccess ||
-        h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->variant, h->stream) != cudaSuccess ||
+        h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->variant, fused ? cur : nullptr,
+                       fused ? cur + h->N : nullptr, fused ? nxt : nullptr, fused ? nxt + h->N : nullptr, h->flag,
+                       h->stream) != cudaSuccess ||
         cudaEventRecord(e[2], h->stream) != cudaSuccess ||
-        (outflow && h->ks->outflow(h->pop, h->G, h->P, (int)((t + 1) & 1), h->top, h->stream) != cudaSuccess) ||
+        (outflow && h->ks->outflow(h->pop, h->G, h->P, layout ^ 1, h->top, fused ? nxt : nullptr,
+                                   fused ? nxt + h->N : nullptr, h->stream) != cudaSuccess) ||
         cudaEventRecord(e[3], h->stream) != cudaSuccess) {
       st = fail(h, LBM_ECUDA, "profiled step launch: %s", cudaGetErrorString(cudaGetLastError()));
       break;
@@ -554,8 +620,10 @@ long long lbm_time(const lbm* h) { return h ? h->t : -1; }
 
 int lbm_kernels_per_step(const lbm* h) {
   if (!h) return -1;
-  return 2 + (h->p.bc[5] == LBM_BC_OUTFLOW ? 1 : 0);
+  return (h->variant == 3 ? 1 : 2) + (h->p.bc[5] == LBM_BC_OUTFLOW ? 1 : 0);
 }
+
+int lbm_kernel_variant(const lbm* h) { return h ? h->variant : -1; }
 
 const char* lbm_last_error(const lbm* h) { return h ? h->err.c_str() : "NULL handle"; }
 
@@ -619,15 +687,12 @@ lbm_status lbm_selfcheck(const char** msg) {
 lbm_status lbm_autotune(lbm* h, int steps, int* chosen) {
   if (!h) return LBM_EINVAL;
   if (steps < 1) return fail(h, LBM_EINVAL, "steps must be >= 1");
-  const bool two = h->ks->has_paired && h->nx % 2 == 0;
-  if (!two) {
-    h->variant = 1;
-    lbm_status st = lbm_step(h, steps);
-    if (st != LBM_OK) return st;
-    if (chosen) *chosen = 1;
-    return lbm_synchronize(h);
-  }
-  float ms[2] = {0.f, 0.f};
+  if (h->unstable) return fail(h, LBM_EUNSTABLE, "watchdog: non-finite or non-positive density seen");
+  int cand[3], nc = 0;
+  cand[nc++] = 1;
+  if (h->ks->has_paired && h->nx % 2 == 0) cand[nc++] = 2;
+  if (h->ks->has_fused) cand[nc++] = 3;
+  float ms[3] = {0.f, 0.f, 0.f};
   cudaEvent_t e0, e1;
   LBM_CUDA(h, cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -635,22 +700,28 @@ lbm_status lbm_autotune(lbm* h, int steps, int* chosen) {
     return fail(h, LBM_ECUDA, "cudaEventCreate failed");
   }
   lbm_status st = LBM_OK;
-  for (int v = 1; v <= 2 && st == LBM_OK; ++v) {
-    h->variant = v;
-    // direct launches: both kernels timed the same way, no graph capture in between
-    if (cudaEventRecord(e0, h->stream) != cudaSuccess) st = fail(h, LBM_ECUDA, "cudaEventRecord failed");
+  for (int c = 0; c < nc && st == LBM_OK; ++c) {
+    h->variant = cand[c];
+    st = ensure_fix(h, h->stream);  // untimed: only needed when entering the fused pass
+    // direct launches: every kernel timed the same way, no graph capture in between
+    if (st == LBM_OK && cudaEventRecord(e0, h->stream) != cudaSuccess)
+      st = fail(h, LBM_ECUDA, "cudaEventRecord failed");
     for (int k = 0; k < steps && st == LBM_OK; ++k) {
       st = enqueue_step(h, h->t, h->stream);
       if (st == LBM_OK) h->t += 1;
     }
     if (st == LBM_OK && (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                         cudaEventElapsedTime(&ms[v - 1], e0, e1) != cudaSuccess))
+                         cudaEventElapsedTime(&ms[c], e0, e1) != cudaSuccess))
       st = fail(h, LBM_ECUDA, "autotune timing: %s", cudaGetErrorString(cudaGetLastError()));
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != LBM_OK) return st;
-  h->variant = ms[1] < ms[0] ? 2 : 1;
+  int best = 0;
+  for (int c = 1; c < nc; ++c)
+    if (ms[c] < ms[best]) best = c;
+  if (h->variant != cand[best]) h->fix_ready = false;
+  h->variant = cand[best];
   drop_graphs(h);  // captured graphs hold the kernel of the previous choice
   if (chosen) *chosen = h->variant;
   return check_flag(h);
@@ -770,6 +841,10 @@ lbm_status lbm_batch_step(lbm_batch* b, int n) {
     if (cudaEventRecord(b->ready[i], b->h[i]->stream) != cudaSuccess ||
         cudaStreamWaitEvent(b->stream, b->ready[i], 0) != cudaSuccess)
       return LBM_ECUDA;
+  }
+  for (lbm* h : b->h) {
+    lbm_status st = ensure_fix(h, b->stream);
+    if (st != LBM_OK) return st;
   }
   int k = 0;
   if (n >= kGraphSteps) {

@@ -473,6 +473,7 @@ struct Recol {
   R frac;        // rho_r / rho
   R n0, n1, n2;  // unit normal grad(phi)/|grad(phi)| (0 where undefined)
   R rc[4];       // beta rho_r rho_b / rho * varphi_i(alpha_bar) / |c_i| per speed class (rc[0] unused)
+  R rho;         // rho of the node (watchdog of the fused density pass)
   typename MaskOf<R>::type has_n;
 };
 
@@ -576,6 +577,7 @@ __device__ __forceinline__ Recol<R> collide(const KConst<R>& K, const R fr[27], 
   const R abar = K.a_mid + K.a_half * phi;
   const R cr = K.beta * rho_r * rho_b * inv_rho * R(27.0 / 19.0) * (R(1) - abar);
   out.frac = rho_r * inv_rho;
+  out.rho = rho;
   out.rc[0] = R(0);
   out.rc[1] = cr * R(weight_of(tensor_index(1, 0, 0)));
   out.rc[2] = cr * R(weight_of(tensor_index(1, 1, 0)) * 0.70710678118654752440);
@@ -609,6 +611,117 @@ __device__ __forceinline__ int wrap_or_clamp(int q, int n, int bc_lo, int bc_hi)
   return q;
 }
 
+// ---------------------------------------------------------------------------
+// Fused density pass.  The density of node y at t+1 is the sum of the
+// populations streamed into it, rho_k(y, t+1) = sum_i f*_i^k(y - c_i, t)
+// (boundaries: y is the owner of the slot S(x, i)), so the collide-stream
+// kernel of step t can accumulate the next step's (rho, rho_r) while it writes
+// f*, and the separate density pass (which rereads every population) is not
+// needed.  Accumulators are fixed point, value * 2^22 in int32 (|value| < 512,
+// resolution 2.4e-7): integer addition is exact and associative, so the
+// atomics of different blocks give bitwise reproducible sums in any order.
+constexpr float kFixScale = 4194304.0f;
+constexpr float kFixInv = 1.0f / 4194304.0f;
+__device__ __forceinline__ int to_fix(float v) { return __float2int_rn(v * kFixScale); }
+
+struct FusedIO {
+  const int* cur_rho;  // fixed-point rho and rho_r of the step's input state (index dnode)
+  const int* cur_red;
+  int* nxt_rho;        // accumulators of the next state (zero on entry)
+  int* nxt_red;
+  int* flag;           // watchdog
+};
+
+// (rho, phi) of a density-tile cell from the fixed-point accumulators; the
+// Dirichlet inlet nodes carry rho_r0 and phi = 1 (as in pass 1)
+__device__ __forceinline__ float2 fused_cell(const FusedIO& io, int64_t i) {
+  const float rho = (float)io.cur_rho[i] * kFixInv, rr = (float)io.cur_red[i] * kFixInv;
+  return make_float2(rho, __fdividef(rr + rr - rho, rho));
+}
+
+// Per-warp rows of next-step densities: warp w (one x-row of the block) owns
+// prow[w][K][c] = (rho, rho_r) for its 9 target rows K = (dy+1) + 3(dz+1) and
+// the TX columns c = target x - (x0 - 1); columns 0 and TX-1 take what leaves the
+// block's x range (the flush maps them through the x faces).  Every entry is
+// written once per step, so nothing needs clearing and no atomics are needed.
+constexpr int NWARPS = NTHREADS / 32;
+
+// red part of f*_T (the recolouring of emit)
+template <int T, bool RECOL, typename R>
+__device__ __forceinline__ R red_part(R fstar, const Recol<R>& rc) {
+  if (T == REST || !RECOL) return rc.frac * fstar;
+  return fma_(rc.rc[speed2_of(T)], cdot<T>(rc.n0, rc.n1, rc.n2), rc.frac * fstar);
+}
+
+// Fast rows (a warp is one x-row whose y/z neighbours are inside the box, all
+// lanes active): the directions (-1|0|+1, dy, dz) = 3K, 3K+1, 3K+2 of the warp
+// all land in the target row (y+dy, z+dz); lane l's target x0+l collects
+// z(l) + p(l-1) + m(l+1), summed with two shuffles; lanes 0 and 31 also write
+// m(0) / p(31) into the edge columns.
+template <int K, bool RECOL, typename R>
+__device__ __forceinline__ void fused_row(float2* prow, const R f[27], const Recol<R>& rc) {
+  const int lane = threadIdx.x;
+  const float mt = f[3 * K], zt = f[3 * K + 1], pt = f[3 * K + 2];
+  const float mr = red_part<3 * K, RECOL>(f[3 * K], rc), zr = red_part<3 * K + 1, RECOL>(f[3 * K + 1], rc),
+              pr = red_part<3 * K + 2, RECOL>(f[3 * K + 2], rc);
+  const float pt_in = __shfl_up_sync(0xffffffffu, pt, 1), pr_in = __shfl_up_sync(0xffffffffu, pr, 1);
+  const float mt_in = __shfl_down_sync(0xffffffffu, mt, 1), mr_in = __shfl_down_sync(0xffffffffu, mr, 1);
+  float st = zt, sr = zr;
+  if (lane > 0) {
+    st += pt_in;
+    sr += pr_in;
+  }
+  if (lane < 31) {
+    st += mt_in;
+    sr += mr_in;
+  }
+  float2* row = prow + (((threadIdx.y + BY * threadIdx.z) * 9 + K) * TX);
+  row[lane + 1] = make_float2(st, sr);
+  if (lane == 0) row[0] = make_float2(mt, mr);
+  if (lane == 31) row[TX - 1] = make_float2(pt, pr);
+}
+
+// target coordinate along one axis of the slot S(x, t) (c: the component of c_t)
+__device__ __forceinline__ void axis_target(int& q, int p, int c, int n, int bc_lo, int bc_hi, bool& bounce,
+                                            bool& ghost) {
+  if (c == 0) return;
+  if (q < 0) {
+    if (bc_lo == BC_PERIODIC) q = n - 1;
+    else if (bc_lo == BC_NOSLIP) bounce = true;
+    else q = p;  // specular reflection keeps the coordinate
+  } else if (q >= n) {
+    if (bc_hi == BC_PERIODIC) q = 0;
+    else if (bc_hi == BC_NOSLIP) bounce = true;
+    else if (bc_hi == BC_OUTFLOW) ghost = true;
+    else q = p;
+  }
+}
+
+// Other rows (next to a y or z face, or boxes without fast rows): direction T
+// goes straight into the global accumulators of the owner of its slot S(x, T)
+// (bounced back to x, reflected, wrapped, or into the ghost plane above an
+// outflow face, which no node reads as a density).
+template <int T, typename R>
+__device__ __forceinline__ void fused_node(const Geom& G, const FusedIO& io, int x, int y, int z, const R f[27],
+                                           const Recol<R>& rc) {
+  constexpr int dx = cx_of(T), dy = cy_of(T), dz = cz_of(T);
+  int tx = x + dx, ty = y + dy, tz = z + dz;
+  bool bounce = false, ghost = false;
+  axis_target(tx, x, dx, G.nx, G.bc[0], G.bc[1], bounce, ghost);
+  axis_target(ty, y, dy, G.ny, G.bc[2], G.bc[3], bounce, ghost);
+  axis_target(tz, z, dz, G.nz, G.bc[4], G.bc[5], bounce, ghost);
+  if (bounce) {
+    tx = x;
+    ty = y;
+    tz = z;
+  } else if (ghost) {
+    return;
+  }
+  const int64_t i = dnode(G, tx, ty, tz);
+  atomicAdd(io.nxt_rho + i, to_fix((float)f[T]));
+  atomicAdd(io.nxt_red + i, to_fix((float)red_part<T, true>(f[T], rc)));
+}
+
 // write direction T of the node (step parity `odd`): colours, f* and red fraction.
 // RECOL: some node of the warp has an interface normal (otherwise the
 // recolouring term is zero and the red fraction of every direction is rho_r/rho).
@@ -639,32 +752,41 @@ __device__ __forceinline__ void emit(const Store& st, const KConst<R>& K, const 
   }
 }
 
-template <int T, class Store, typename R, bool FAST, bool RECOL>
+// FUSED: after each direction (fast rows: each triple of directions), add it to the
+// next step's densities (fused density pass; sacc, io as in k_collide_stream)
+template <int T, class Store, typename R, bool FAST, bool RECOL, bool FUSED>
 struct EmitLoop {
   __device__ __forceinline__ static void run(const Store& st, const KConst<R>& K, const Geom& G, const NodeMap& nm,
-                                             const AoRow& ar, bool odd, const R* f, const Recol<R>& rc) {
+                                             const AoRow& ar, bool odd, const R* f, const Recol<R>& rc,
+                                             float2* prow, const FusedIO& io, int x, int y, int z) {
     emit<T, FAST, RECOL>(st, K, G, nm, ar, odd, f, rc);
-    EmitLoop<T + 1, Store, R, FAST, RECOL>::run(st, K, G, nm, ar, odd, f, rc);
+    if constexpr (FUSED) {
+      if constexpr (FAST) {
+        if constexpr (T % 3 == 2) fused_row<T / 3, RECOL>(prow, f, rc);
+      } else {
+        fused_node<T>(G, io, x, y, z, f, rc);
+      }
+    }
+    EmitLoop<T + 1, Store, R, FAST, RECOL, FUSED>::run(st, K, G, nm, ar, odd, f, rc, prow, io, x, y, z);
   }
 };
-template <class Store, typename R, bool FAST, bool RECOL>
-struct EmitLoop<27, Store, R, FAST, RECOL> {
+template <class Store, typename R, bool FAST, bool RECOL, bool FUSED>
+struct EmitLoop<27, Store, R, FAST, RECOL, FUSED> {
   __device__ __forceinline__ static void run(const Store&, const KConst<R>&, const Geom&, const NodeMap&,
-                                             const AoRow&, bool, const R*, const Recol<R>&) {}
+                                             const AoRow&, bool, const R*, const Recol<R>&, float2*, const FusedIO&,
+                                             int, int, int) {}
 };
 
 // ---------------------------------------------------------------------------
-// pass 1: density / phase field
-template <class Store>
+// pass 1: density / phase field.  FIX: write the fixed-point accumulators of
+// the fused density pass instead (priming the fused pass from a stored state).
+template <class Store, bool FIX>
 __global__ void __launch_bounds__(NTHREADS) k_density(Store st, Geom G,
                                                       const __grid_constant__ KConst<typename DensOf<Store>::real> K,
                                                       int layout, typename DensOf<Store>::type* __restrict__ dens,
-                                                      int* __restrict__ flag, long long* __restrict__ step_counter) {
+                                                      int* __restrict__ flag, int* __restrict__ fix_rho,
+                                                      int* __restrict__ fix_red) {
   using D = typename DensOf<Store>::real;
-  // the counter holds the index of the step being taken (read by pass 2's inlet noise)
-  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0 &&
-      threadIdx.z == 0)
-    *step_counter += 1;
   const int x = blockIdx.x * BX + threadIdx.x;
   const int y = blockIdx.y * BY + threadIdx.y;
   const int z = blockIdx.z * BZ + threadIdx.z;
@@ -685,36 +807,53 @@ __global__ void __launch_bounds__(NTHREADS) k_density(Store st, Geom G,
     rr += fr[t];
     rt += ft[t];
   }
-  D rb = rt - rr;
-  if (is_inlet(G, x, y, z)) {
-    rr = (D)K.rho_r0_d;
-    rb = D(0);
+  if (!(rt > D(0)) || !(rt < D(1e30))) atomicOr(flag, 1);
+  if constexpr (FIX) {
+    fix_rho[dnode(G, x, y, z)] = to_fix((float)rt);
+    fix_red[dnode(G, x, y, z)] = to_fix((float)rr);
+  } else {
+    D rb = rt - rr;
+    if (is_inlet(G, x, y, z)) {
+      rr = (D)K.rho_r0_d;
+      rb = D(0);
+    }
+    const D rho = rr + rb;
+    typename DensOf<Store>::type v;
+    v.x = rho;
+    v.y = (rr - rb) / rho;
+    dens[dnode(G, x, y, z)] = v;
   }
-  const D rho = rr + rb;
-  if (!(rho > D(0)) || !(rho < D(1e30))) atomicOr(flag, 1);
-  typename DensOf<Store>::type v;
-  v.x = rho;
-  v.y = (rr - rb) / rho;
-  dens[dnode(G, x, y, z)] = v;
 }
 
-// pass 2: gradients + collision + perturbation + recolouring + in-place streaming
-template <class Store, int MINB>
+// pass 2: gradients + collision + perturbation + recolouring + in-place streaming.
+// counter[t & 1] holds the index t of the step (read by the inlet noise); the
+// kernel writes t + 1 into counter[(t + 1) & 1] for the next step, so a
+// captured graph of steps needs no parameter updates.  FUSED: (rho, phi) come
+// from the fixed-point accumulators of the previous step, and the kernel
+// accumulates those of the next step (FusedRows, FusedNodes).
+template <class Store, int MINB, bool FUSED>
 __global__ void __launch_bounds__(NTHREADS, MINB)
     k_collide_stream(Store st, const __grid_constant__ Geom G,
                      const __grid_constant__ KConst<typename DensOf<Store>::real> K, int odd,
-                     const typename DensOf<Store>::type* __restrict__ dens, const long long* __restrict__ step_counter) {
+                     const typename DensOf<Store>::type* __restrict__ dens, long long* __restrict__ counter,
+                     const FusedIO io) {
   using R = typename DensOf<Store>::real;  // compute type: FP64 for FP64 storage, FP32 otherwise
   using DT = typename DensOf<Store>::type;
   __shared__ DT tile[TILE];
+  __shared__ float2 prow[FUSED ? NWARPS * 9 * TX : 1];
+  __shared__ int pfast[NWARPS];
 
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * BZ;
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
   const bool active = x < G.nx && y < G.ny && z < G.nz;
+  const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
+  const long long step = counter[odd];
+  if (tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) counter[odd ^ 1] = step + 1;
 
   R fr[27], ft[27];
   // a warp is one x-row of the block: the fast-row test is warp-uniform
   const bool fast = fast_row(G, y, z);
+  if (FUSED && threadIdx.x == 0) pfast[tid >> 5] = active && fast;
   const int64_t base = snode(G, x, y, z);
   AoRow ar;
   if (fast) ar.init<Store::PLANES>(G, x, y, z);
@@ -731,10 +870,11 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
   // halo tile of (rho, phi): warp w fills rows w, w+8, w+16 of the TY*TZ rows of TX
   // values; lanes cover x0-1 .. x0+30 and lanes 0..1 also x0+31, x0+32.
   {
-    const int warp = (threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z)) >> 5, lane = threadIdx.x;
+    const int warp = tid >> 5, lane = threadIdx.x;
     const int xa = wrap_or_clamp(x0 + lane - 1, G.nx, G.bc[0], G.bc[1]);
     const int xb = wrap_or_clamp(x0 + lane + 31, G.nx, G.bc[0], G.bc[1]);
     const int cxa = xa < G.nx ? xa : G.nx - 1, cxb = xb < G.nx ? xb : G.nx - 1;
+    const float rho_r0f = (float)K.rho_r0_d;
 #pragma unroll
     for (int k = 0; k < (TY * TZ + NTHREADS / 32 - 1) / (NTHREADS / 32); ++k) {
       const int row = warp + k * (NTHREADS / 32);
@@ -743,51 +883,132 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
         const int gy = wrap_or_clamp(y0 + ty - 1, G.ny, G.bc[2], G.bc[3]);
         const int gz = wrap_or_clamp(z0 + tz - 1, G.nz, G.bc[4], G.bc[5]);
         // out-of-box tail rows of a ragged block read a clamped in-box row
-        const int64_t rbase = (int64_t)G.nx * ((int64_t)(gy < G.ny ? gy : G.ny - 1) +
-                                                (int64_t)G.ny * (gz < G.nz ? gz : G.nz - 1));
-        tile[row * TX + lane] = dens[rbase + cxa];
-        if (lane < TX - 32) tile[row * TX + 32 + lane] = dens[rbase + cxb];
+        const int cy = gy < G.ny ? gy : G.ny - 1, cz = gz < G.nz ? gz : G.nz - 1;
+        const int64_t rbase = (int64_t)G.nx * ((int64_t)cy + (int64_t)G.ny * cz);
+        if constexpr (FUSED) {
+          tile[row * TX + lane] = fused_cell(io, rbase + cxa);
+          if (lane < TX - 32) tile[row * TX + 32 + lane] = fused_cell(io, rbase + cxb);
+        } else {
+          tile[row * TX + lane] = dens[rbase + cxa];
+          if (lane < TX - 32) tile[row * TX + 32 + lane] = dens[rbase + cxb];
+        }
+      }
+    }
+    if constexpr (FUSED) {
+      if (G.inflow && z0 == 0) {
+        // the Dirichlet inlet nodes carry rho_r0 and phi = 1, as in pass 1; tile planes 0 (z = -1,
+        // mirrored onto z = 0) and 1 (z = 0).  Block-uniform branch.
+        __syncthreads();
+        for (int c = tid; c < TX * TY; c += NTHREADS) {
+          int gx = wrap_or_clamp(x0 + c % TX - 1, G.nx, G.bc[0], G.bc[1]);
+          int gy = wrap_or_clamp(y0 + c / TX - 1, G.ny, G.bc[2], G.bc[3]);
+          gx = gx < G.nx ? gx : G.nx - 1;
+          gy = gy < G.ny ? gy : G.ny - 1;
+          if (is_inlet(G, gx, gy, 0)) {
+            tile[c] = make_float2(rho_r0f, 1.0f);
+            tile[c + TX * TY] = make_float2(rho_r0f, 1.0f);
+          }
+        }
       }
     }
   }
   __syncthreads();
-  if (!active) return;
+  if (!FUSED && !active) return;
 
-  R gphi[3] = {R(0), R(0), R(0)}, grho[3] = {R(0), R(0), R(0)};
-  const int lx = threadIdx.x + 1, ly = threadIdx.y + 1, lz = threadIdx.z + 1;
+  if (active) {
+    R gphi[3] = {R(0), R(0), R(0)}, grho[3] = {R(0), R(0), R(0)};
+    const int lx = threadIdx.x + 1, ly = threadIdx.y + 1, lz = threadIdx.z + 1;
 #pragma unroll
-  for (int t = 0; t < 27; ++t) {
-    if (t == REST) continue;
-    const DT v = tile[(lx + cx_of(t)) + TX * ((ly + cy_of(t)) + TY * (lz + cz_of(t)))];
-    const R w3 = R(3.0 * weight_of(t));
-    const R a = w3 * (R)v.y, b = w3 * (R)v.x;
-    if (cx_of(t) != 0) { gphi[0] += R(cx_of(t)) * a; grho[0] += R(cx_of(t)) * b; }
-    if (cy_of(t) != 0) { gphi[1] += R(cy_of(t)) * a; grho[1] += R(cy_of(t)) * b; }
-    if (cz_of(t) != 0) { gphi[2] += R(cz_of(t)) * a; grho[2] += R(cz_of(t)) * b; }
+    for (int t = 0; t < 27; ++t) {
+      if (t == REST) continue;
+      const DT v = tile[(lx + cx_of(t)) + TX * ((ly + cy_of(t)) + TY * (lz + cz_of(t)))];
+      const R w3 = R(3.0 * weight_of(t));
+      const R a = w3 * (R)v.y, b = w3 * (R)v.x;
+      if (cx_of(t) != 0) { gphi[0] += R(cx_of(t)) * a; grho[0] += R(cx_of(t)) * b; }
+      if (cy_of(t) != 0) { gphi[1] += R(cy_of(t)) * a; grho[1] += R(cy_of(t)) * b; }
+      if (cz_of(t) != 0) { gphi[2] += R(cz_of(t)) * a; grho[2] += R(cz_of(t)) * b; }
+    }
+
+    R f[27];
+    Recol<R> rc;
+    if (is_inlet(G, x, y, z)) {
+      inlet_state(K, dnode(G, x, y, z), (int64_t)step, f);
+      rc.frac = R(1);
+      rc.n0 = rc.n1 = rc.n2 = R(0);
+      rc.rc[0] = rc.rc[1] = rc.rc[2] = rc.rc[3] = R(0);
+      rc.rho = R(1);
+      rc.has_n = false;
+    } else {
+      rc = collide(K, fr, ft, gphi, grho, f);
+    }
+    if constexpr (FUSED) {
+      // the watchdog of pass 1, on the density this step starts from
+      if (!(rc.rho > R(0)) || !(rc.rho < R(1e30))) atomicOr(io.flag, 1);
+    }
+    // warp-uniform: does any node of the warp carry an interface normal?
+    const bool recol = __any_sync(__activemask(), any_(rc.has_n));
+    NodeMap nm;
+    if (fast) {
+      if (recol) EmitLoop<0, Store, R, true, true, FUSED>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
+      else EmitLoop<0, Store, R, true, false, FUSED>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
+    } else {
+      if (odd) nm.init(G, x, y, z);
+      else nm.base = base;  // the even step only uses the base
+      if (recol) EmitLoop<0, Store, R, false, true, FUSED>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
+      else EmitLoop<0, Store, R, false, false, FUSED>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
+    }
   }
 
-  R f[27];
-  Recol<R> rc;
-  if (is_inlet(G, x, y, z)) {
-    inlet_state(K, dnode(G, x, y, z), (int64_t)*step_counter, f);
-    rc.frac = R(1);
-    rc.n0 = rc.n1 = rc.n2 = R(0);
-    rc.rc[0] = rc.rc[1] = rc.rc[2] = rc.rc[3] = R(0);
-    rc.has_n = false;
-  } else {
-    rc = collide(K, fr, ft, gphi, grho, f);
-  }
-  // warp-uniform: does any node of the warp carry an interface normal?
-  const bool recol = __any_sync(__activemask(), any_(rc.has_n));
-  NodeMap nm;
-  if (fast) {
-    if (recol) EmitLoop<0, Store, R, true, true>::run(st, K, G, nm, ar, odd != 0, f, rc);
-    else EmitLoop<0, Store, R, true, false>::run(st, K, G, nm, ar, odd != 0, f, rc);
-  } else {
-    if (odd) nm.init(G, x, y, z);
-    else nm.base = base;  // the even step only uses the base
-    if (recol) EmitLoop<0, Store, R, false, true>::run(st, K, G, nm, ar, odd != 0, f, rc);
-    else EmitLoop<0, Store, R, false, false>::run(st, K, G, nm, ar, odd != 0, f, rc);
+  if constexpr (FUSED) {
+    // merge the warps' rows into the global accumulators: tile row (ty, tz) (target y = y0-1+ty,
+    // z = z0-1+tz) sums, in a fixed order, row K = (ty-wy) + 3(tz-wz) of every fast warp (wy, wz)
+    // within one row of it; warp w takes tile rows w, w+8, w+16, lanes the columns
+    __syncthreads();
+    const int warp = tid >> 5, lane = threadIdx.x;
+    int gxa = x0 - 1 + lane, gxb = x0 + 31 + lane;  // lanes 0..1 also take columns 32, 33
+    if (gxa < 0) gxa = G.bc[0] == BC_PERIODIC ? G.nx - 1 : 0;
+    if (gxb >= G.nx) gxb = G.bc[1] == BC_PERIODIC ? gxb - G.nx : G.nx - 1;
+    const bool ina = gxa < G.nx, inb = lane < TX - 32 && gxb >= 0 && gxb < G.nx;
+#pragma unroll
+    for (int k = 0; k < (TY * TZ + NWARPS - 1) / NWARPS; ++k) {
+      const int row = warp + k * NWARPS;
+      if (row < TY * TZ) {
+        const int ty = row % TY, tz = row / TY;
+        const int gy = y0 - 1 + ty, gz = z0 - 1 + tz;
+        if (gy >= 0 && gy < G.ny && gz >= 0 && gz < G.nz) {
+          float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int wz = 0; wz < BZ; ++wz) {
+#pragma unroll
+            for (int wy = 0; wy < BY; ++wy) {
+              const int ky = ty - wy, kz = tz - wz;
+              if (ky >= 0 && ky <= 2 && kz >= 0 && kz <= 2 && pfast[wy + BY * wz]) {
+                const float2* src = prow + ((wy + BY * wz) * 9 + ky + 3 * kz) * TX;
+                const float2 u = src[lane];
+                a.x += u.x;
+                a.y += u.y;
+                if (lane < TX - 32) {
+                  const float2 v = src[32 + lane];
+                  b.x += v.x;
+                  b.y += v.y;
+                }
+              }
+            }
+          }
+          const int64_t rb = (int64_t)G.nx * ((int64_t)gy + (int64_t)G.ny * gz);
+          const int ar = to_fix(a.x), aq = to_fix(a.y);
+          if (ina && (ar | aq)) {
+            atomicAdd(io.nxt_rho + rb + gxa, ar);
+            atomicAdd(io.nxt_red + rb + gxa, aq);
+          }
+          const int br = to_fix(b.x), bq = to_fix(b.y);
+          if (inb && (br | bq)) {
+            atomicAdd(io.nxt_rho + rb + gxb, br);
+            atomicAdd(io.nxt_red + rb + gxb, bq);
+          }
+        }
+      }
+    }
   }
 }
 
@@ -844,9 +1065,13 @@ struct EmitLoop2<27, Store> {
 template <class Store, int MINB>
 __global__ void __launch_bounds__(PTHREADS, MINB)
     k_collide_stream2(Store st, const __grid_constant__ Geom G, const __grid_constant__ KConst<F2> K, int odd,
-                      const float2* __restrict__ dens, const long long* __restrict__ step_counter) {
+                      const float2* __restrict__ dens, long long* __restrict__ counter) {
   __shared__ float2 tile[TILE];
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * PY, z0 = blockIdx.z * PZ;
+  const long long step = counter[odd];  // step index protocol of k_collide_stream
+  if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0 && blockIdx.x == 0 && blockIdx.y == 0 &&
+      blockIdx.z == 0)
+    counter[odd ^ 1] = step + 1;
   const int xa = x0 + 2 * threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
   const bool active = xa < G.nx && y < G.ny && z < G.nz;  // nx even: xa + 1 < nx as well
 
@@ -927,7 +1152,7 @@ __global__ void __launch_bounds__(PTHREADS, MINB)
         Ks.seed = K.seed;
         Ks.rho_r0_d = K.rho_r0_d;
         Ks.alpha_r_d = K.alpha_r_d;
-        inlet_state(Ks, dnode(G, xa + lane, y, z), (int64_t)*step_counter, fin);
+        inlet_state(Ks, dnode(G, xa + lane, y, z), (int64_t)step, fin);
 #pragma unroll
         for (int t = 0; t < 27; ++t) {
           if (lane == 0) f[t].v.x = fin[t]; else f[t].v.y = fin[t];
@@ -957,7 +1182,8 @@ __device__ __forceinline__ void store_pair(const Store& st, const KConst<R>& K, 
 // produced time t+1; `layout` is the layout of time t+1.
 template <class Store>
 __global__ void k_outflow(Store st, Geom G, const __grid_constant__ KConst<typename DensOf<Store>::real> K,
-                          int layout, typename DensOf<Store>::real* __restrict__ top) {
+                          int layout, typename DensOf<Store>::real* __restrict__ top, int* __restrict__ fix_rho,
+                          int* __restrict__ fix_red) {
   using R = typename DensOf<Store>::real;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -988,6 +1214,7 @@ __global__ void k_outflow(Store st, Geom G, const __grid_constant__ KConst<typen
   const R uz = (mz + R(0.5) * F[2]) / rho;
   const R lam = uz > R(0) ? uz : R(0);
   const R inv = R(1) / (R(1) + lam);
+  R sr = R(0), st_ = R(0);
 #pragma unroll
   for (int t = 0; t < 27; ++t) {
     R* tr = top + (int64_t)t * Pn + pp;
@@ -996,10 +1223,17 @@ __global__ void k_outflow(Store st, Geom G, const __grid_constant__ KConst<typen
     const R nb = (*tb + lam * fb[t]) * inv;
     *tr = nr;
     *tb = nb;
+    sr += nr;
+    st_ += nr + nb;
     int64_t node;
     int dir;
     slot_of(here, layout, t, node, dir);
     store_pair(st, K, node, dir, nr, nb);
+  }
+  // fused density pass: the plane's new populations replace what the collide-stream kernel accumulated
+  if (fix_rho) {
+    fix_rho[dnode(G, x, y, G.nz - 1)] = to_fix((float)st_);
+    fix_red[dnode(G, x, y, G.nz - 1)] = to_fix((float)sr);
   }
 }
 

@@ -38,28 +38,47 @@ struct Launch {
   using R = typename DensOf<Store>::real;
   static KConst<R> kc(const Phys& P) { return make_kconst<R>(P); }
 
-  static cudaError_t density(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag,
-                             long long* step, cudaStream_t s) {
-    k_density<Store><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(Tr::make(pop, G), G, kc(P), layout, static_cast<DT*>(dens),
-                                                           flag, step);
-    return cudaGetLastError();
-  }
-  static cudaError_t collide(void* pop, const Geom& G, const Phys& P, int odd, const void* dens, const long long* step,
-                             int variant, cudaStream_t s) {
-    if constexpr (Tr::paired) {
-      if (variant == 2) {
-        k_collide_stream2<Store, Tr::minb2><<<grid3(G), dim3(PX, PY, PZ), 0, s>>>(
-            Tr::make(pop, G), G, make_kconst<F2>(P), odd, static_cast<const float2*>(dens), step);
+  static constexpr bool fused = !std::is_same<R, double>::value;
+
+  static cudaError_t density(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag, int* fix_rho,
+                             int* fix_red, cudaStream_t s) {
+    if constexpr (fused) {
+      if (fix_rho) {
+        k_density<Store, true><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(Tr::make(pop, G), G, kc(P), layout,
+                                                                     static_cast<DT*>(dens), flag, fix_rho, fix_red);
         return cudaGetLastError();
       }
     }
-    k_collide_stream<Store, Tr::minb><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(Tr::make(pop, G), G, kc(P), odd,
-                                                                            static_cast<const DT*>(dens), step);
+    k_density<Store, false><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(Tr::make(pop, G), G, kc(P), layout,
+                                                                  static_cast<DT*>(dens), flag, nullptr, nullptr);
     return cudaGetLastError();
   }
-  static cudaError_t outflow(void* pop, const Geom& G, const Phys& P, int layout, void* top, cudaStream_t s) {
+  static cudaError_t collide(void* pop, const Geom& G, const Phys& P, int odd, const void* dens, long long* counter,
+                             int variant, const int* cur_rho, const int* cur_red, int* nxt_rho, int* nxt_red,
+                             int* flag, cudaStream_t s) {
+    if constexpr (Tr::paired) {
+      if (variant == 2) {
+        k_collide_stream2<Store, Tr::minb2><<<grid3(G), dim3(PX, PY, PZ), 0, s>>>(
+            Tr::make(pop, G), G, make_kconst<F2>(P), odd, static_cast<const float2*>(dens), counter);
+        return cudaGetLastError();
+      }
+    }
+    FusedIO io{cur_rho, cur_red, nxt_rho, nxt_red, flag};
+    if constexpr (fused) {
+      if (variant == 3) {
+        k_collide_stream<Store, Tr::minb, true><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(
+            Tr::make(pop, G), G, kc(P), odd, static_cast<const DT*>(dens), counter, io);
+        return cudaGetLastError();
+      }
+    }
+    k_collide_stream<Store, Tr::minb, false><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(
+        Tr::make(pop, G), G, kc(P), odd, static_cast<const DT*>(dens), counter, io);
+    return cudaGetLastError();
+  }
+  static cudaError_t outflow(void* pop, const Geom& G, const Phys& P, int layout, void* top, int* fix_rho,
+                             int* fix_red, cudaStream_t s) {
     dim3 b(32, 4), g((unsigned)((G.nx + 31) / 32), (unsigned)((G.ny + 3) / 4));
-    k_outflow<Store><<<g, b, 0, s>>>(Tr::make(pop, G), G, kc(P), layout, static_cast<R*>(top));
+    k_outflow<Store><<<g, b, 0, s>>>(Tr::make(pop, G), G, kc(P), layout, static_cast<R*>(top), fix_rho, fix_red);
     return cudaGetLastError();
   }
   static cudaError_t init(void* pop, const Geom& G, const Phys& P, const double* rr, const double* rb, const double* u,
@@ -99,7 +118,7 @@ struct Launch {
         (std::is_same<Store, PlainStore<double>>::value || std::is_same<Store, PlainStore<float>>::value) ? 2 : 1,
         sizeof(DT),
         sizeof(R),
-        &density, &collide, &outflow, &init, &get_pop, &set_pop, &top_from_state, &macro, Tr::paired};
+        &density, &collide, &outflow, &init, &get_pop, &set_pop, &top_from_state, &macro, Tr::paired, fused};
     return &ks;
   }
 };

@@ -27,7 +27,7 @@ SYMBOLS = ["lbm_workspace_size", "lbm_create", "lbm_init_fields", "lbm_set_inflo
            "lbm_diag", "lbm_get_populations", "lbm_set_populations", "lbm_profile_step", "lbm_set_stream", "lbm_synchronize", "lbm_time",
            "lbm_kernels_per_step", "lbm_last_error", "lbm_status_string", "lbm_moment_matrix", "lbm_selfcheck",
            "lbm_diag_fields_static", "lbm_autotune", "lbm_batch_create", "lbm_batch_step", "lbm_batch_synchronize",
-           "lbm_batch_free", "lbm_measure_fp32_peak", "lbm_free"]
+           "lbm_batch_free", "lbm_measure_fp32_peak", "lbm_kernel_variant", "lbm_free"]
 
 
 class LbmError(RuntimeError):
@@ -81,6 +81,7 @@ def library():
         lib.lbm_time.argtypes = [h]
         lib.lbm_time.restype = ctypes.c_longlong
         lib.lbm_kernels_per_step.argtypes = [h]
+        lib.lbm_kernel_variant.argtypes = [h]
         lib.lbm_last_error.argtypes = [h]
         lib.lbm_last_error.restype = ctypes.c_char_p
         lib.lbm_status_string.argtypes = [i]
@@ -252,6 +253,11 @@ class Lattice:
     @property
     def kernels_per_step(self):
         return library().lbm_kernels_per_step(self._h)
+
+    @property
+    def variant(self):
+        """Collide-stream kernel in use: 1 one node per thread, 2 two nodes, 3 fused density pass."""
+        return library().lbm_kernel_variant(self._h)
 
     def set_stream(self, stream):
         self.stream = stream

@@ -48,8 +48,9 @@ def test_fp64_matches_oracle_100_steps(cuda, name):
 
 
 def _variants(name):
-    """Pass-2 kernels to test on a case: one node per thread, and two per thread where nx is even."""
-    return [1, 2] if CASES[name][0]["shape"][0] % 2 == 0 else [1]
+    """Pass-2 kernels to test on a case: one node per thread, two per thread where nx is even, and
+    one per thread with the fused density pass."""
+    return [1, 2, 3] if CASES[name][0]["shape"][0] % 2 == 0 else [1, 3]
 
 
 @pytest.mark.parametrize("name,variant", [(n, v) for n in CASES for v in _variants(n)])
@@ -70,7 +71,7 @@ def test_fp32_matches_oracle(cuda, name, variant):
     lat.close()
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 @pytest.mark.parametrize("name", ["static_droplet_32", "rayleigh_taylor_16", "jet_32x20x40"])
 def test_packed_storage_error_budget(cuda, name, storage, variant):
@@ -106,6 +107,46 @@ def test_one_and_two_nodes_per_thread_agree(cuda, storage):
     tol = 2e-5 if storage == "f32" else 2e-3
     assert np.max(np.abs(ra - rb_)) < tol and np.max(np.abs(ba - bb)) < tol
     assert np.max(np.abs(ua - ub)) < 50 * tol * np.max(np.abs(ua))
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_fused_density_pass_matches_two_pass(cuda, storage):
+    """The fused density pass accumulates the next step's densities from f* before it is stored
+    (fixed point, 2^-22), the two-pass scheme sums the stored populations: the densities entering
+    the gradients differ by rounding only.  After 100 steps the fields agree to the FP32 budget
+    (2e-5) or the half-storage budget (2e-3)."""
+    work, u_amp = CASES["jet_32x20x40"]
+    rr, rb, u = L.initial_fields(work, seed=5, u_amp=0.01)
+    a = pkg.Lattice(work["shape"], work["params"], storage=storage, variant=1)
+    b = pkg.Lattice(work["shape"], work["params"], storage=storage, variant=3)
+    for lat in (a, b):
+        lat.init_fields(rr, rb, u)
+        lat.step(100)
+    ra, ba, ua = a.macro()
+    rf, bf, uf = b.macro()
+    tol = 2e-5 if storage == "f32" else 2e-3
+    assert np.max(np.abs(ra - rf)) < tol and np.max(np.abs(ba - bf)) < tol
+    assert np.max(np.abs(ua - uf)) < 50 * tol * np.max(np.abs(ua))
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("name", ["ragged_mixed", "rayleigh_taylor_16", "jet_32x20x40"])
+def test_fused_density_pass_is_reproducible(cuda, name):
+    """Integer accumulation: runs of the fused pass agree bit for bit, across graph replays and
+    direct launches (the atomics of different blocks land in a different order every run)."""
+    work, u_amp = CASES[name]
+    rr, rb, u = L.initial_fields(work, seed=3, u_amp=u_amp)
+    a = pkg.Lattice(work["shape"], work["params"], storage="f32", variant=3)
+    b = pkg.Lattice(work["shape"], work["params"], storage="f32", variant=3)
+    a.init_fields(rr, rb, u)
+    b.init_fields(rr, rb, u)
+    a.step(37)
+    for _ in range(37):
+        b.step(1)
+    np.testing.assert_array_equal(a.get_populations(), b.get_populations())
     a.close()
     b.close()
 
