@@ -14,3 +14,4 @@ from .lbm import (Batch, Lattice, LbmError, STORAGE, SYMBOLS, library, moment_ma
                   measure_fp32_peak,
                   BC_PERIODIC, BC_NOSLIP, BC_FREESLIP, BC_INFLOW_WALL, BC_OUTFLOW)
 from .build import build as build_library  # noqa: F401
+from .mlp import Mlp  # noqa: F401

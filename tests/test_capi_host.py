@@ -23,11 +23,15 @@ def lib():
 
 
 def test_header_symbols_exported(lib):
-    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
-    declared = set(re.findall(r"LBM_EXPORT[^;(]*?\b(lbm_\w+)\s*\(", text))
-    assert declared == set(binding.SYMBOLS)
-    for name in declared:
-        assert hasattr(lib, name), name
+    from paper_1705_03141_gb300 import mlp
+
+    for header, names in (("lbm.h", binding.SYMBOLS), ("lbm_mlp.h", mlp.MLP_SYMBOLS)):
+        text = open(os.path.join(ROOT, "include", header)).read()
+        declared = set(re.findall(r"LBM_EXPORT[^;(]*?\b(lbm_\w+)\s*\(", text))
+        assert declared == set(names), header
+        for name in declared:
+            assert hasattr(lib, name), name
+    assert sorted(os.listdir(os.path.join(ROOT, "include"))) == ["lbm.h", "lbm_mlp.h"]
 
 
 def test_selfcheck_and_moment_matrix(lib):
