@@ -220,6 +220,38 @@ def cpu_oracle_sample(seconds_budget=20.0, nz_sample=32, seed=1234, steps=None):
     return nodes * steps / dt / 1e6, oracle.num_threads(), steps, nodes, dt
 
 
+def oracle_configs(seconds=5.0):
+    """FP64 oracle throughput on the validation set-ups, on one host thread and on all of them:
+    the 32^3 static droplet and the 64^3 oscillating droplet in full, the jet as its bottom 16
+    planes (same nozzle, walls, outflow); about `seconds` of stepping per entry, scaled to MLUPS."""
+    import oracle
+
+    full = oracle.num_threads()
+    cases = [("static_droplet_32x32x32", L.static_droplet()), ("oscillating_droplet_64x64x64",
+                                                              L.oscillating_droplet()),
+             ("jet_128x128x512_bottom16_planes", L.jet(nz=16))]
+    out = {}
+    try:
+        for name, w in cases:
+            if name.startswith("static"):
+                w["params"]["s"] = L.uniform_rates(1.0)  # the tau = 1 droplet runs with unit rates (R17)
+            rr, rb, u = L.initial_fields(w)
+            for threads in (1, full):
+                oracle.lib().orc_set_threads(threads)
+                o = oracle.Oracle(w["shape"], w["params"])
+                o.init_fields(rr, rb, u)
+                t0 = time.perf_counter()
+                o.step(1)
+                steps = max(1, int(seconds / max(time.perf_counter() - t0, 1e-6)))
+                t0 = time.perf_counter()
+                o.step(steps)
+                dt = time.perf_counter() - t0
+                out[f"{name}_threads{threads}"] = {"mlups": o.N * steps / dt / 1e6, "steps": steps, "nodes": o.N}
+    finally:
+        oracle.lib().orc_set_threads(full)
+    return out
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle as it stands, on the host cores, on a bounded sample of
     the jet workload (its bottom planes, same nozzle, walls and outflow) sized so that warm-up and
@@ -309,6 +341,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--oracle-configs", action="store_true",
+                    help="also time the oracle on the droplet set-ups and a jet sample, 1 and all threads")
     ap.add_argument("--variant", type=int, default=0, help="collide-stream kernel: 0 library choice, 1 one node "
                     "per thread, 2 two nodes per thread, 3 fused density pass")
     args = ap.parse_args()
@@ -403,7 +437,8 @@ def main():
     traffic = profiled_traffic(args.storage, variant)
     fp32_peak = max(pkg.measure_fp32_peak(False), pkg.measure_fp32_peak(True))
     roof = {"bound": "hbm", "kernel": "k_collide_stream", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+            "frac": achieved / peak, "peak_kind": peak_kind, "frac_of_nominal_7900": achieved / 7900.0,
+            "traffic": traffic,
             "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": ms[1],
             "variant": variant, "density_pass_ms": ms[0], "outflow_ms": ms[2],
             "step_share_collide": ms[1] / max(sum(ms), 1e-12),
@@ -418,6 +453,8 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"jet workload cut to its bottom 32 planes ({nodes} nodes), {st} FP64 oracle steps "
                          f"from rest ({cdt:.1f} s)"}
+        if args.oracle_configs:
+            cpu["configs"] = oracle_configs()
 
     if rank == 0:
         line = {"metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
