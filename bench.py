@@ -76,7 +76,7 @@ def kernel_hash():
 
 
 def profile_name(storage, variant):
-    return f"collide_stream{'_fused' if variant == 3 else ''}_jet_{storage}.md"
+    return f"collide_stream{ {3: '_fused', 4: '_pipelined'}.get(variant, '') }_jet_{storage}.md"
 
 
 def collide_bytes(storage, variant):
@@ -344,7 +344,7 @@ def main():
     ap.add_argument("--oracle-configs", action="store_true",
                     help="also time the oracle on the droplet set-ups and a jet sample, 1 and all threads")
     ap.add_argument("--variant", type=int, default=0, help="collide-stream kernel: 0 library choice, 1 one node "
-                    "per thread, 2 two nodes per thread, 3 fused density pass")
+                    "per thread, 2 two nodes per thread, 3 fused density pass, 4 software-pipelined (packed)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -132,11 +132,15 @@ typedef struct {
                             storage and an even nx), 3 = one node per thread with
                             the fused density pass: the collide-stream kernel also
                             accumulates the next step's densities, so the separate
-                            density pass is skipped (needs F32/F16/BF16 storage).
-                            Variants 1 and 2 compute identical results; variant 3
-                            differs from them only by the rounding of the densities
-                            that enter the gradients, and is bitwise reproducible.
-                            F32/F16/BF16 storage needs rho_r0, rho_b0 <= 64. */
+                            density pass is skipped (needs F32/F16/BF16 storage),
+                            4 = one node per thread, software-pipelined: persistent
+                            blocks copy the next tile's populations into shared
+                            memory while computing the current one (needs F16/BF16
+                            storage).  All variants compute the same update; they
+                            differ in FP32 rounding (variant 3 also rounds the
+                            densities that enter the gradients to fixed point), and
+                            each is bitwise reproducible.  F32/F16/BF16 storage needs
+                            rho_r0, rho_b0 <= 64. */
 } lbm_params;
 
 typedef struct lbm lbm; /* opaque handle; owns all device state it allocated */
@@ -214,7 +218,7 @@ LBM_EXPORT long long lbm_time(const lbm* h);
  * pass also enqueues one memset per step, not counted). */
 LBM_EXPORT int lbm_kernels_per_step(const lbm* h);
 
-/* The collide-stream kernel variant the handle runs (1, 2 or 3; see
+/* The collide-stream kernel variant the handle runs (1 to 4; see
  * lbm_params.variant and lbm_autotune); -1 for NULL. */
 LBM_EXPORT int lbm_kernel_variant(const lbm* h);
 
@@ -236,11 +240,11 @@ LBM_EXPORT lbm_status lbm_selfcheck(const char** msg);
 
 /* Pick the fastest collide-stream kernel for this handle by measurement: take
  * `steps` steps (>= 1) with each available variant (1; 2 where the storage and
- * nx allow; 3 for F32/F16/BF16 storage), timed with CUDA events on the
- * handle's stream, keep the fastest for later steps and report it in *chosen
- * (1, 2 or 3; may be NULL).  The tuning steps are ordinary time steps of the
- * same update, so the time advances by steps times the number of variants
- * tried (1 for F64 storage, 2 or 3 otherwise).  Synchronises. */
+ * nx allow; 3 for F32/F16/BF16 storage; 4 for F16/BF16 storage), timed with
+ * CUDA events on the handle's stream, keep the fastest for later steps and
+ * report it in *chosen (1 to 4; may be NULL).  The tuning steps are ordinary
+ * time steps of the same update, so the time advances by steps times the
+ * number of variants tried.  Synchronises. */
 LBM_EXPORT lbm_status lbm_autotune(lbm* h, int steps, int* chosen);
 
 /* Batched stepping of several independent boxes (e.g. the jets of a regime

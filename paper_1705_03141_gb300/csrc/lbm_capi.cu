@@ -41,7 +41,7 @@ struct lbm {
   char* ws;
   bool own_ws;
   void *pop, *dens, *top, *partial;
-  int* fix[2];      // fused density pass: [rho | rho_r] fixed-point accumulators of the state at an even / odd step
+  unsigned long long* fix[2];  // fused density pass: packed fixed-point (rho, rho_r) of the state at an even / odd step
   bool fix_ready;   // fix[t & 1] holds the densities of the current state
   long long* counter;  // [2]: step index, see k_collide_stream
   int* flag;
@@ -113,7 +113,9 @@ const char* validate(int nx, int ny, int nz, const lbm_params* p) {
     if (p->bc[f] == LBM_BC_OUTFLOW && f != 5) return "OUTFLOW is only allowed on the +z face";
   }
   if (p->storage < 0 || p->storage > 3) return "unknown storage";
-  if (p->variant < 0 || p->variant > 3) return "unknown kernel variant";
+  if (p->variant < 0 || p->variant > 4) return "unknown kernel variant";
+  if (p->variant == 4 && p->storage != LBM_STORE_F16 && p->storage != LBM_STORE_BF16)
+    return "the software-pipelined kernel needs packed (F16/BF16) storage";
   if (p->variant == 2 && (p->storage == LBM_STORE_F64 || nx % 2 != 0))
     return "the two-nodes-per-thread kernel needs FP32 arithmetic (not F64 storage) and an even nx";
   if (p->variant == 3 && p->storage == LBM_STORE_F64)
@@ -184,27 +186,24 @@ lbm_status enqueue_step(lbm* h, long long t, cudaStream_t s) {
   const bool outflow = h->p.bc[5] == LBM_BC_OUTFLOW;
   if (h->variant == 3) {
     // fused density pass: no pass 1; the accumulators of t+1 start from zero
-    int *cur = h->fix[layout], *nxt = h->fix[layout ^ 1];
-    LBM_CUDA(h, cudaMemsetAsync(nxt, 0, sizeof(int) * 2 * (size_t)h->N, s));
-    LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, 3, cur, cur + h->N, nxt,
-                               nxt + h->N, h->flag, s));
-    if (outflow)
-      LBM_CUDA(h, h->ks->outflow(h->pop, h->G, h->P, layout ^ 1, h->top, nxt, nxt + h->N, s));
+    unsigned long long *cur = h->fix[layout], *nxt = h->fix[layout ^ 1];
+    LBM_CUDA(h, cudaMemsetAsync(nxt, 0, sizeof(unsigned long long) * (size_t)h->N, s));
+    LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, 3, cur, nxt, h->flag, s));
+    if (outflow) LBM_CUDA(h, h->ks->outflow(h->pop, h->G, h->P, layout ^ 1, h->top, nxt, s));
     return LBM_OK;
   }
   h->fix_ready = false;  // steps without the fused pass leave its accumulators behind
-  LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, nullptr, nullptr, s));
-  LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->variant, nullptr, nullptr, nullptr,
-                             nullptr, h->flag, s));
-  if (outflow) LBM_CUDA(h, h->ks->outflow(h->pop, h->G, h->P, layout ^ 1, h->top, nullptr, nullptr, s));
+  LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, nullptr, s));
+  LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->variant, nullptr, nullptr,
+                             h->flag, s));
+  if (outflow) LBM_CUDA(h, h->ks->outflow(h->pop, h->G, h->P, layout ^ 1, h->top, nullptr, s));
   return LBM_OK;
 }
 
 // before fused steps from a state the fused pass did not produce: fill the accumulators of step t
 lbm_status ensure_fix(lbm* h, cudaStream_t s) {
   if (h->variant != 3 || h->fix_ready) return LBM_OK;
-  int* cur = h->fix[h->t & 1];
-  LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, (int)(h->t & 1), h->dens, h->flag, cur, cur + h->N, s));
+  LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, (int)(h->t & 1), h->dens, h->flag, h->fix[h->t & 1], s));
   h->fix_ready = true;
   return LBM_OK;
 }
@@ -340,8 +339,8 @@ lbm_status lbm_create(int nx, int ny, int nz, const lbm_params* p, lbm** out) {
   }
   h->pop = h->ws + h->L.pop;
   h->dens = h->ws + h->L.dens;
-  h->fix[0] = reinterpret_cast<int*>(h->ws + h->L.fix);
-  h->fix[1] = h->fix[0] + 2 * h->N;
+  h->fix[0] = reinterpret_cast<unsigned long long*>(h->ws + h->L.fix);
+  h->fix[1] = h->fix[0] + h->N;
   h->top = h->ws + h->L.top;
   h->counter = reinterpret_cast<long long*>(h->ws + h->L.counter);
   h->flag = reinterpret_cast<int*>(h->ws + h->L.flag);
@@ -565,20 +564,19 @@ lbm_status lbm_profile_step(lbm* h, int n, double* ms_out) {
     cudaEvent_t* e = ev + per * k;
     // the same launches as enqueue_step, with an event between them; with the fused density
     // pass the first interval is the clearing of the next step's accumulators
-    int* cur = h->fix[layout];
-    int* nxt = h->fix[layout ^ 1];
-    const size_t nfix = sizeof(int) * 2 * (size_t)h->N;
+    unsigned long long* cur = h->fix[layout];
+    unsigned long long* nxt = h->fix[layout ^ 1];
+    const size_t nfix = sizeof(unsigned long long) * (size_t)h->N;
     if (cudaEventRecord(e[0], h->stream) != cudaSuccess ||
         (fused ? cudaMemsetAsync(nxt, 0, nfix, h->stream)
-               : h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, nullptr, nullptr, h->stream)) !=
+               : h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, nullptr, h->stream)) !=
             cudaSuccess ||
         cudaEventRecord(e[1], h->stream) != cudaSuccess ||
         h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->variant, fused ? cur : nullptr,
-                       fused ? cur + h->N : nullptr, fused ? nxt : nullptr, fused ? nxt + h->N : nullptr, h->flag,
-                       h->stream) != cudaSuccess ||
+                       fused ? nxt : nullptr, h->flag, h->stream) != cudaSuccess ||
         cudaEventRecord(e[2], h->stream) != cudaSuccess ||
-        (outflow && h->ks->outflow(h->pop, h->G, h->P, layout ^ 1, h->top, fused ? nxt : nullptr,
-                                   fused ? nxt + h->N : nullptr, h->stream) != cudaSuccess) ||
+        (outflow && h->ks->outflow(h->pop, h->G, h->P, layout ^ 1, h->top, fused ? nxt : nullptr, h->stream) !=
+                        cudaSuccess) ||
         cudaEventRecord(e[3], h->stream) != cudaSuccess) {
       st = fail(h, LBM_ECUDA, "profiled step launch: %s", cudaGetErrorString(cudaGetLastError()));
       break;
@@ -688,11 +686,12 @@ lbm_status lbm_autotune(lbm* h, int steps, int* chosen) {
   if (!h) return LBM_EINVAL;
   if (steps < 1) return fail(h, LBM_EINVAL, "steps must be >= 1");
   if (h->unstable) return fail(h, LBM_EUNSTABLE, "watchdog: non-finite or non-positive density seen");
-  int cand[3], nc = 0;
+  int cand[4], nc = 0;
   cand[nc++] = 1;
   if (h->ks->has_paired && h->nx % 2 == 0) cand[nc++] = 2;
   if (h->ks->has_fused) cand[nc++] = 3;
-  float ms[3] = {0.f, 0.f, 0.f};
+  if (h->ks->has_pipelined) cand[nc++] = 4;
+  float ms[4] = {0.f, 0.f, 0.f, 0.f};
   cudaEvent_t e0, e1;
   LBM_CUDA(h, cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {

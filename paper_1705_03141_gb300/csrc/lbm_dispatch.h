@@ -12,19 +12,18 @@ struct KernelSet {
   int pop_planes;         // stored planes per direction (2 plain, 1 packed)
   size_t dens_bytes;      // bytes per node of the pass-1 field
   size_t real_bytes;      // bytes of the compute type (outflow plane history)
-  // pass 1; with fix_rho/fix_red non-null it writes the fixed-point accumulators of the fused
-  // density pass instead of dens (priming the fused pass from a stored state)
-  cudaError_t (*density)(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag, int* fix_rho,
-                         int* fix_red, cudaStream_t s);
+  // pass 1; with fix non-null it writes the fixed-point accumulators of the fused density pass
+  // instead of dens (priming the fused pass from a stored state)
+  cudaError_t (*density)(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag, void* fix,
+                         cudaStream_t s);
   // pass 2.  variant: 1 = one node per thread, 2 = two nodes per thread (FP32 arithmetic, nx even),
-  // 3 = one node per thread with the fused density pass (reads cur_*, accumulates into nxt_*, which
-  // must be zero).  counter: the two-entry step index of k_collide_stream.
+  // 3 = one node per thread with the fused density pass (reads cur, accumulates into nxt, which
+  // must be zero), 4 = software-pipelined one node per thread (packed storage).  counter: the
+  // two-entry step index of k_collide_stream.
   cudaError_t (*collide)(void* pop, const Geom& G, const Phys& P, int odd, const void* dens, long long* counter,
-                         int variant, const int* cur_rho, const int* cur_red, int* nxt_rho, int* nxt_red, int* flag,
-                         cudaStream_t s);
-  // convective outflow; with fix_rho/fix_red non-null it also rewrites the top plane's accumulators
-  cudaError_t (*outflow)(void* pop, const Geom& G, const Phys& P, int layout, void* top, int* fix_rho, int* fix_red,
-                         cudaStream_t s);
+                         int variant, const void* cur, void* nxt, int* flag, cudaStream_t s);
+  // convective outflow; with fix non-null it also rewrites the top plane's accumulators
+  cudaError_t (*outflow)(void* pop, const Geom& G, const Phys& P, int layout, void* top, void* fix, cudaStream_t s);
   cudaError_t (*init)(void* pop, const Geom& G, const Phys& P, const double* rr, const double* rb, const double* u,
                       cudaStream_t s);
   cudaError_t (*get_pop)(void* pop, const Geom& G, const Phys& P, int layout, int pdir, double* out_r, double* out_b,
@@ -36,6 +35,7 @@ struct KernelSet {
                        cudaStream_t s);
   bool has_paired;        // a two-nodes-per-thread pass 2 exists for this storage
   bool has_fused;         // a fused-density pass 2 exists for this storage (FP32 arithmetic)
+  bool has_pipelined;     // a software-pipelined pass 2 exists for this storage (packed)
 };
 
 const KernelSet* kernels_f64();

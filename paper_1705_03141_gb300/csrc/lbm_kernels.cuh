@@ -617,25 +617,31 @@ __device__ __forceinline__ int wrap_or_clamp(int q, int n, int bc_lo, int bc_hi)
 // (boundaries: y is the owner of the slot S(x, i)), so the collide-stream
 // kernel of step t can accumulate the next step's (rho, rho_r) while it writes
 // f*, and the separate density pass (which rereads every population) is not
-// needed.  Accumulators are fixed point, value * 2^22 in int32 (|value| < 512,
-// resolution 2.4e-7): integer addition is exact and associative, so the
-// atomics of different blocks give bitwise reproducible sums in any order.
+// needed.  Accumulators are fixed point, value * 2^22 (resolution 2.4e-7):
+// integer addition is exact and associative, so the atomics of different
+// blocks give bitwise reproducible sums in any order.  One 64-bit word per node
+// holds both, rho_r * 2^54 + rho * 2^22 in two's complement: every partial sum
+// is added as one 64-bit integer, and since the total rho * 2^22 lies in
+// [0, 2^32) (rho < 1024), the low 32 bits return rho and the high 32 bits
+// rho_r (|rho_r| < 512) exactly, whatever the signs of the partial sums.
 constexpr float kFixScale = 4194304.0f;
 constexpr float kFixInv = 1.0f / 4194304.0f;
 __device__ __forceinline__ int to_fix(float v) { return __float2int_rn(v * kFixScale); }
+__device__ __forceinline__ unsigned long long pack_fix(float rho, float rho_r) {
+  return ((unsigned long long)(unsigned)to_fix(rho_r) << 32) + (unsigned long long)(long long)to_fix(rho);
+}
 
 struct FusedIO {
-  const int* cur_rho;  // fixed-point rho and rho_r of the step's input state (index dnode)
-  const int* cur_red;
-  int* nxt_rho;        // accumulators of the next state (zero on entry)
-  int* nxt_red;
-  int* flag;           // watchdog
+  const unsigned long long* cur;  // fixed-point (rho, rho_r) of the step's input state (index dnode)
+  unsigned long long* nxt;        // accumulators of the next state (zero on entry)
+  int* flag;                      // watchdog
 };
 
 // (rho, phi) of a density-tile cell from the fixed-point accumulators; the
 // Dirichlet inlet nodes carry rho_r0 and phi = 1 (as in pass 1)
 __device__ __forceinline__ float2 fused_cell(const FusedIO& io, int64_t i) {
-  const float rho = (float)io.cur_rho[i] * kFixInv, rr = (float)io.cur_red[i] * kFixInv;
+  const unsigned long long v = io.cur[i];
+  const float rho = (float)(unsigned)v * kFixInv, rr = (float)(int)(unsigned)(v >> 32) * kFixInv;
   return make_float2(rho, __fdividef(rr + rr - rho, rho));
 }
 
@@ -717,9 +723,7 @@ __device__ __forceinline__ void fused_node(const Geom& G, const FusedIO& io, int
   } else if (ghost) {
     return;
   }
-  const int64_t i = dnode(G, tx, ty, tz);
-  atomicAdd(io.nxt_rho + i, to_fix((float)f[T]));
-  atomicAdd(io.nxt_red + i, to_fix((float)red_part<T, true>(f[T], rc)));
+  atomicAdd(io.nxt + dnode(G, tx, ty, tz), pack_fix((float)f[T], (float)red_part<T, true>(f[T], rc)));
 }
 
 // write direction T of the node (step parity `odd`): colours, f* and red fraction.
@@ -784,8 +788,8 @@ template <class Store, bool FIX>
 __global__ void __launch_bounds__(NTHREADS) k_density(Store st, Geom G,
                                                       const __grid_constant__ KConst<typename DensOf<Store>::real> K,
                                                       int layout, typename DensOf<Store>::type* __restrict__ dens,
-                                                      int* __restrict__ flag, int* __restrict__ fix_rho,
-                                                      int* __restrict__ fix_red) {
+                                                      int* __restrict__ flag,
+                                                      unsigned long long* __restrict__ fix) {
   using D = typename DensOf<Store>::real;
   const int x = blockIdx.x * BX + threadIdx.x;
   const int y = blockIdx.y * BY + threadIdx.y;
@@ -809,8 +813,7 @@ __global__ void __launch_bounds__(NTHREADS) k_density(Store st, Geom G,
   }
   if (!(rt > D(0)) || !(rt < D(1e30))) atomicOr(flag, 1);
   if constexpr (FIX) {
-    fix_rho[dnode(G, x, y, z)] = to_fix((float)rt);
-    fix_red[dnode(G, x, y, z)] = to_fix((float)rr);
+    fix[dnode(G, x, y, z)] = pack_fix((float)rt, (float)rr);
   } else {
     D rb = rt - rr;
     if (is_inlet(G, x, y, z)) {
@@ -996,20 +999,177 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
             }
           }
           const int64_t rb = (int64_t)G.nx * ((int64_t)gy + (int64_t)G.ny * gz);
-          const int ar = to_fix(a.x), aq = to_fix(a.y);
-          if (ina && (ar | aq)) {
-            atomicAdd(io.nxt_rho + rb + gxa, ar);
-            atomicAdd(io.nxt_red + rb + gxa, aq);
-          }
-          const int br = to_fix(b.x), bq = to_fix(b.y);
-          if (inb && (br | bq)) {
-            atomicAdd(io.nxt_rho + rb + gxb, br);
-            atomicAdd(io.nxt_red + rb + gxb, bq);
-          }
+          const unsigned long long av = pack_fix(a.x, a.y), bv = pack_fix(b.x, b.y);
+          if (ina && av) atomicAdd(io.nxt + rb + gxa, av);
+          if (inb && bv) atomicAdd(io.nxt + rb + gxb, bv);
         }
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// pass 2, software-pipelined (packed storage).  A persistent block walks over
+// the tiles of the box; while it computes one tile, the next tile's population
+// words (the same slots the one-node kernel loads) and its (rho, phi) halo are
+// already on their way into shared memory through asynchronous copies
+// (cp.async), so the collision does not wait on memory latency.  Two stages
+// of 27 x 256 words + the halo tile: 68 KB per block, 3 blocks per SM.
+constexpr int PF_POP = 27 * NTHREADS;
+constexpr int PF_STAGE_BYTES = PF_POP * 4 + TILE * 8;
+constexpr int PF_SMEM = 2 * PF_STAGE_BYTES;
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// word index of direction t's post-streaming value of a node on a fast row (step parity odd)
+template <int T>
+__device__ __forceinline__ int64_t fast_src(const Geom& G, const AoRow& ar, int odd) {
+  if (!odd) return ar.e[1] + T * 32;
+  return ar.slot0<26 - T, 27>(G) + (26 - T) * 32;
+}
+template <int T>
+struct PfIssueFast {
+  __device__ __forceinline__ static void run(const uint32_t* A, const Geom& G, const AoRow& ar, int odd,
+                                             uint32_t* pop_s, int tid) {
+    cp_async4(pop_s + T * NTHREADS + tid, A + fast_src<T>(G, ar, odd));
+    PfIssueFast<T + 1>::run(A, G, ar, odd, pop_s, tid);
+  }
+};
+template <>
+struct PfIssueFast<27> {
+  __device__ __forceinline__ static void run(const uint32_t*, const Geom&, const AoRow&, int, uint32_t*, int) {}
+};
+
+// start the copies of tile (x0, y0, z0) into one stage
+__device__ __forceinline__ void pf_issue(const uint32_t* A, const Geom& G, const float2* __restrict__ dens, int odd,
+                                         int x0, int y0, int z0, uint32_t* pop_s, float2* tile_s) {
+  const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
+  if (x < G.nx && y < G.ny && z < G.nz) {
+    if (fast_row(G, y, z)) {
+      AoRow ar;
+      ar.init<27>(G, x, y, z);
+      PfIssueFast<0>::run(A, G, ar, odd, pop_s, tid);
+    } else {
+      NodeMap nm;
+      nm.init(G, x, y, z);
+#pragma unroll
+      for (int t = 0; t < 27; ++t) {
+        int64_t node;
+        int dir;
+        slot_of(nm, odd, t, node, dir);
+        cp_async4(pop_s + t * NTHREADS + tid, A + elem_index(node, 27, dir));
+      }
+    }
+  }
+  const int warp = tid >> 5, lane = threadIdx.x;
+  const int xa = wrap_or_clamp(x0 + lane - 1, G.nx, G.bc[0], G.bc[1]);
+  const int xb = wrap_or_clamp(x0 + lane + 31, G.nx, G.bc[0], G.bc[1]);
+  const int cxa = xa < G.nx ? xa : G.nx - 1, cxb = xb < G.nx ? xb : G.nx - 1;
+#pragma unroll
+  for (int k = 0; k < (TY * TZ + NWARPS - 1) / NWARPS; ++k) {
+    const int row = warp + k * NWARPS;
+    if (row < TY * TZ) {
+      const int gy = wrap_or_clamp(y0 + row % TY - 1, G.ny, G.bc[2], G.bc[3]);
+      const int gz = wrap_or_clamp(z0 + row / TY - 1, G.nz, G.bc[4], G.bc[5]);
+      const int64_t rbase = (int64_t)G.nx * ((int64_t)(gy < G.ny ? gy : G.ny - 1) +
+                                              (int64_t)G.ny * (gz < G.nz ? gz : G.nz - 1));
+      cp_async8(tile_s + row * TX + lane, dens + rbase + cxa);
+      if (lane < TX - 32) cp_async8(tile_s + row * TX + 32 + lane, dens + rbase + cxb);
+    }
+  }
+}
+
+template <class Store, int MINB>
+__global__ void __launch_bounds__(NTHREADS, MINB)
+    k_collide_stream_pf(Store st, const __grid_constant__ Geom G, const __grid_constant__ KConst<float> K, int odd,
+                        const float2* __restrict__ dens, long long* __restrict__ counter, int ntx, int nty,
+                        int ntiles) {
+  static_assert(Store::PLANES == 27, "packed storage only");
+  extern __shared__ __align__(16) unsigned char pf_smem[];
+  // stage k: words at pf_smem + k * PF_STAGE_BYTES, halo tile after them
+#define PF_POP_S(k) reinterpret_cast<uint32_t*>(pf_smem + (k) * PF_STAGE_BYTES)
+#define PF_TILE_S(k) reinterpret_cast<float2*>(pf_smem + (k) * PF_STAGE_BYTES + PF_POP * 4)
+  const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
+  const long long step = counter[odd];  // step index protocol of k_collide_stream
+  if (tid == 0 && blockIdx.x == 0) counter[odd ^ 1] = step + 1;
+
+  int tile = blockIdx.x;
+  if (tile < ntiles)
+    pf_issue(st.A, G, dens, odd, (tile % ntx) * BX, ((tile / ntx) % nty) * BY, (tile / (ntx * nty)) * BZ,
+             PF_POP_S(0), PF_TILE_S(0));
+  cp_async_commit();
+  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+    const int nxt = tile + gridDim.x;
+    if (nxt < ntiles)
+      pf_issue(st.A, G, dens, odd, (nxt % ntx) * BX, ((nxt / ntx) % nty) * BY, (nxt / (ntx * nty)) * BZ,
+               PF_POP_S((it + 1) & 1), PF_TILE_S((it + 1) & 1));
+    cp_async_commit();
+    cp_async_wait_prev();  // this tile's copies (all but the group just issued) have landed
+    __syncthreads();
+    const uint32_t* ps = PF_POP_S(it & 1);
+    const float2* ts = PF_TILE_S(it & 1);
+    const int x0 = (tile % ntx) * BX, y0 = ((tile / ntx) % nty) * BY, z0 = (tile / (ntx * nty)) * BZ;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
+    if (x < G.nx && y < G.ny && z < G.nz) {
+      float fr[27], ft[27];
+#pragma unroll
+      for (int t = 0; t < 27; ++t)
+        Store::decode(ps[t * NTHREADS + tid], K.refB[speed2_of(t)], speed2_of(t) == 0 ? K.dref[0] : 0.0f, fr[t],
+                      ft[t]);
+      float gphi[3] = {0.f, 0.f, 0.f}, grho[3] = {0.f, 0.f, 0.f};
+      const int lx = threadIdx.x + 1, ly = threadIdx.y + 1, lz = threadIdx.z + 1;
+#pragma unroll
+      for (int t = 0; t < 27; ++t) {
+        if (t == REST) continue;
+        const float2 v = ts[(lx + cx_of(t)) + TX * ((ly + cy_of(t)) + TY * (lz + cz_of(t)))];
+        const float w3 = float(3.0 * weight_of(t));
+        const float a = w3 * v.y, b = w3 * v.x;
+        if (cx_of(t) != 0) { gphi[0] += float(cx_of(t)) * a; grho[0] += float(cx_of(t)) * b; }
+        if (cy_of(t) != 0) { gphi[1] += float(cy_of(t)) * a; grho[1] += float(cy_of(t)) * b; }
+        if (cz_of(t) != 0) { gphi[2] += float(cz_of(t)) * a; grho[2] += float(cz_of(t)) * b; }
+      }
+      float f[27];
+      Recol<float> rc;
+      if (is_inlet(G, x, y, z)) {
+        inlet_state(K, dnode(G, x, y, z), (int64_t)step, f);
+        rc.frac = 1.0f;
+        rc.n0 = rc.n1 = rc.n2 = 0.0f;
+        rc.rc[0] = rc.rc[1] = rc.rc[2] = rc.rc[3] = 0.0f;
+        rc.rho = 1.0f;
+        rc.has_n = false;
+      } else {
+        rc = collide(K, fr, ft, gphi, grho, f);
+      }
+      const bool recol = __any_sync(__activemask(), rc.has_n);
+      const bool fast = fast_row(G, y, z);
+      NodeMap nm;
+      AoRow ar;
+      FusedIO io{};
+      if (fast) {
+        ar.init<27>(G, x, y, z);
+        if (recol) EmitLoop<0, Store, float, true, true, false>::run(st, K, G, nm, ar, odd != 0, f, rc, nullptr, io, x, y, z);
+        else EmitLoop<0, Store, float, true, false, false>::run(st, K, G, nm, ar, odd != 0, f, rc, nullptr, io, x, y, z);
+      } else {
+        if (odd) nm.init(G, x, y, z);
+        else nm.base = snode(G, x, y, z);
+        if (recol) EmitLoop<0, Store, float, false, true, false>::run(st, K, G, nm, ar, odd != 0, f, rc, nullptr, io, x, y, z);
+        else EmitLoop<0, Store, float, false, false, false>::run(st, K, G, nm, ar, odd != 0, f, rc, nullptr, io, x, y, z);
+      }
+    }
+    __syncthreads();  // the stage is refilled in the next iteration
+  }
+#undef PF_POP_S
+#undef PF_TILE_S
 }
 
 // ---------------------------------------------------------------------------
@@ -1182,8 +1342,8 @@ __device__ __forceinline__ void store_pair(const Store& st, const KConst<R>& K, 
 // produced time t+1; `layout` is the layout of time t+1.
 template <class Store>
 __global__ void k_outflow(Store st, Geom G, const __grid_constant__ KConst<typename DensOf<Store>::real> K,
-                          int layout, typename DensOf<Store>::real* __restrict__ top, int* __restrict__ fix_rho,
-                          int* __restrict__ fix_red) {
+                          int layout, typename DensOf<Store>::real* __restrict__ top,
+                          unsigned long long* __restrict__ fix) {
   using R = typename DensOf<Store>::real;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -1231,9 +1391,8 @@ __global__ void k_outflow(Store st, Geom G, const __grid_constant__ KConst<typen
     store_pair(st, K, node, dir, nr, nb);
   }
   // fused density pass: the plane's new populations replace what the collide-stream kernel accumulated
-  if (fix_rho) {
-    fix_rho[dnode(G, x, y, G.nz - 1)] = to_fix((float)st_);
-    fix_red[dnode(G, x, y, G.nz - 1)] = to_fix((float)sr);
+  if (fix) {
+    fix[dnode(G, x, y, G.nz - 1)] = pack_fix((float)st_, (float)sr);
   }
 }
 

@@ -39,23 +39,23 @@ struct Launch {
   static KConst<R> kc(const Phys& P) { return make_kconst<R>(P); }
 
   static constexpr bool fused = !std::is_same<R, double>::value;
+  static constexpr bool pipelined = Store::PLANES == 27;  // packed storage
 
-  static cudaError_t density(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag, int* fix_rho,
-                             int* fix_red, cudaStream_t s) {
+  static cudaError_t density(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag, void* fix,
+                             cudaStream_t s) {
     if constexpr (fused) {
-      if (fix_rho) {
-        k_density<Store, true><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(Tr::make(pop, G), G, kc(P), layout,
-                                                                     static_cast<DT*>(dens), flag, fix_rho, fix_red);
+      if (fix) {
+        k_density<Store, true><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(
+            Tr::make(pop, G), G, kc(P), layout, static_cast<DT*>(dens), flag, static_cast<unsigned long long*>(fix));
         return cudaGetLastError();
       }
     }
     k_density<Store, false><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(Tr::make(pop, G), G, kc(P), layout,
-                                                                  static_cast<DT*>(dens), flag, nullptr, nullptr);
+                                                                  static_cast<DT*>(dens), flag, nullptr);
     return cudaGetLastError();
   }
   static cudaError_t collide(void* pop, const Geom& G, const Phys& P, int odd, const void* dens, long long* counter,
-                             int variant, const int* cur_rho, const int* cur_red, int* nxt_rho, int* nxt_red,
-                             int* flag, cudaStream_t s) {
+                             int variant, const void* cur, void* nxt, int* flag, cudaStream_t s) {
     if constexpr (Tr::paired) {
       if (variant == 2) {
         k_collide_stream2<Store, Tr::minb2><<<grid3(G), dim3(PX, PY, PZ), 0, s>>>(
@@ -63,7 +63,27 @@ struct Launch {
         return cudaGetLastError();
       }
     }
-    FusedIO io{cur_rho, cur_red, nxt_rho, nxt_red, flag};
+    if constexpr (pipelined) {
+      if (variant == 4) {
+        static bool attr = false;  // first launch per process: allow the 68 KB of dynamic shared memory
+        if (!attr) {
+          cudaError_t e = cudaFuncSetAttribute(k_collide_stream_pf<Store, Tr::minb>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, PF_SMEM);
+          if (e != cudaSuccess) return e;
+          attr = true;
+        }
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const dim3 g3 = grid3(G);
+        const int ntiles = (int)(g3.x * g3.y * g3.z);
+        const int blocks = ntiles < sms * Tr::minb ? ntiles : sms * Tr::minb;
+        k_collide_stream_pf<Store, Tr::minb><<<blocks, dim3(BX, BY, BZ), PF_SMEM, s>>>(
+            Tr::make(pop, G), G, kc(P), odd, static_cast<const float2*>(dens), counter, (int)g3.x, (int)g3.y, ntiles);
+        return cudaGetLastError();
+      }
+    }
+    FusedIO io{static_cast<const unsigned long long*>(cur), static_cast<unsigned long long*>(nxt), flag};
     if constexpr (fused) {
       if (variant == 3) {
         k_collide_stream<Store, Tr::minb, true><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(
@@ -75,10 +95,11 @@ struct Launch {
         Tr::make(pop, G), G, kc(P), odd, static_cast<const DT*>(dens), counter, io);
     return cudaGetLastError();
   }
-  static cudaError_t outflow(void* pop, const Geom& G, const Phys& P, int layout, void* top, int* fix_rho,
-                             int* fix_red, cudaStream_t s) {
+  static cudaError_t outflow(void* pop, const Geom& G, const Phys& P, int layout, void* top, void* fix,
+                             cudaStream_t s) {
     dim3 b(32, 4), g((unsigned)((G.nx + 31) / 32), (unsigned)((G.ny + 3) / 4));
-    k_outflow<Store><<<g, b, 0, s>>>(Tr::make(pop, G), G, kc(P), layout, static_cast<R*>(top), fix_rho, fix_red);
+    k_outflow<Store><<<g, b, 0, s>>>(Tr::make(pop, G), G, kc(P), layout, static_cast<R*>(top),
+                                     static_cast<unsigned long long*>(fix));
     return cudaGetLastError();
   }
   static cudaError_t init(void* pop, const Geom& G, const Phys& P, const double* rr, const double* rb, const double* u,
@@ -118,7 +139,8 @@ struct Launch {
         (std::is_same<Store, PlainStore<double>>::value || std::is_same<Store, PlainStore<float>>::value) ? 2 : 1,
         sizeof(DT),
         sizeof(R),
-        &density, &collide, &outflow, &init, &get_pop, &set_pop, &top_from_state, &macro, Tr::paired, fused};
+        &density, &collide, &outflow, &init, &get_pop, &set_pop, &top_from_state, &macro, Tr::paired, fused,
+        pipelined};
     return &ks;
   }
 };

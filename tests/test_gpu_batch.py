@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 CASES = {name: (w, u) for name, w, u in L.parity_cases()}
 MEMBERS = [("static_droplet_32", "f64", 0), ("jet_32x20x40", "f64", 0), ("ragged_mixed", "f32", 0),
            ("rayleigh_taylor_16", "f16", 0), ("jet_32x20x40", "bf16", 0), ("jet_32x20x40", "f32", 3),
-           ("ragged_mixed", "f16", 3)]
+           ("ragged_mixed", "f16", 3), ("jet_32x20x40", "f16", 4)]
 
 
 def _lattice(name, storage, variant=0, stream=None):
@@ -111,8 +111,10 @@ def test_autotune_keeps_a_valid_state(cuda, storage):
     chosen = lat.autotune(4)
     if storage == "f64":
         assert chosen == 1 and lat.time == 4   # one kernel only in FP64
-    else:
+    elif storage == "f32":
         assert chosen in (1, 2, 3) and lat.time == 12  # one node, two nodes, fused density pass
+    else:
+        assert chosen in (1, 2, 3, 4) and lat.time == 16  # ... and the software-pipelined kernel
     lat.step(100 - lat.time)
     rr, rb, u = L.initial_fields(work, seed=5, u_amp=u_amp)
     orc = oracle.Oracle(work["shape"], work["params"])
