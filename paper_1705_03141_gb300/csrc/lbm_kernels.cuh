@@ -343,10 +343,11 @@ struct PackedStore {
   __device__ __forceinline__ static float code_to_float(uint32_t k) {
     return __uint_as_float(0x4B000000u | k) - 8388608.0f;
   }
-  // word -> (f^r, f); rB, dR: rest-state value of the direction's speed class
+  // word -> (f^r, f); rB, dR: rest-state value of the direction's speed class (dR = 0 for
+  // the moving classes, whose rest value does not depend on q: no multiply for them)
   __device__ __forceinline__ static void decode(uint32_t w, float rB, float dR, float& fr, float& f) {
     const float q = code_to_float(w >> 16) * (1.0f / 65535.0f);
-    f = fmaf(q, dR, rB) + dev_to_float(w);
+    f = (dR != 0.0f ? fmaf(q, dR, rB) : rB) + dev_to_float(w);
     fr = q * f;
   }
   // (f*, q) -> word
@@ -354,7 +355,7 @@ struct PackedStore {
     const float qk = fmaf(__saturatef(q), 65535.0f, 8388608.0f);  // rounds to the nearest code
     const uint32_t k = __float_as_uint(qk) & 0xFFFFu;
     const float qq = (qk - 8388608.0f) * (1.0f / 65535.0f);
-    return (k << 16) | float_to_dev(fstar - fmaf(qq, dR, rB));
+    return (k << 16) | float_to_dev(fstar - (dR != 0.0f ? fmaf(qq, dR, rB) : rB));
   }
   template <typename R>
   __device__ __forceinline__ void load(int64_t node, int dir, int cls, const KConst<R>& K, R& fr, R& ft) const {
