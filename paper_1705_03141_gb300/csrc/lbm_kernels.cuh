@@ -727,6 +727,40 @@ __device__ __forceinline__ void fused_node(const Geom& G, const FusedIO& io, int
   atomicAdd(io.nxt + dnode(G, tx, ty, tz), pack_fix((float)f[T], (float)red_part<T, true>(f[T], rc)));
 }
 
+// grad phi and grad rho at tile cell (lx, ly, lz) from the (rho, phi) halo tile:
+// grad chi = 3 sum_i w_i chi(x + c_i) c_i (the isotropic stencil of Sec. II).
+// w_i depends only on the speed class |c_i|^2: the neighbours of one class are
+// summed first (signs only), then the class weight multiplies once per component.
+template <int CLS, typename R, typename DT>
+__device__ __forceinline__ void class_gradients(const DT* tile, int lx, int ly, int lz, R gphi[3], R grho[3]) {
+  R sp[3] = {R(0), R(0), R(0)}, sr[3] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int t = 0; t < 27; ++t) {
+    if (speed2_of(t) != CLS) continue;
+    const DT v = tile[(lx + cx_of(t)) + TX * ((ly + cy_of(t)) + TY * (lz + cz_of(t)))];
+    if (cx_of(t) > 0) { sp[0] += (R)v.y; sr[0] += (R)v.x; }
+    if (cx_of(t) < 0) { sp[0] -= (R)v.y; sr[0] -= (R)v.x; }
+    if (cy_of(t) > 0) { sp[1] += (R)v.y; sr[1] += (R)v.x; }
+    if (cy_of(t) < 0) { sp[1] -= (R)v.y; sr[1] -= (R)v.x; }
+    if (cz_of(t) > 0) { sp[2] += (R)v.y; sr[2] += (R)v.x; }
+    if (cz_of(t) < 0) { sp[2] -= (R)v.y; sr[2] -= (R)v.x; }
+  }
+  const R w = R(3.0 * weight_of(CLS == 1 ? tensor_index(1, 0, 0) : CLS == 2 ? tensor_index(1, 1, 0) : tensor_index(1, 1, 1)));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    gphi[k] = fma_(w, sp[k], gphi[k]);
+    grho[k] = fma_(w, sr[k], grho[k]);
+  }
+}
+template <typename R, typename DT>
+__device__ __forceinline__ void tile_gradients(const DT* tile, int lx, int ly, int lz, R gphi[3], R grho[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) gphi[k] = grho[k] = R(0);
+  class_gradients<1>(tile, lx, ly, lz, gphi, grho);
+  class_gradients<2>(tile, lx, ly, lz, gphi, grho);
+  class_gradients<3>(tile, lx, ly, lz, gphi, grho);
+}
+
 // write direction T of the node (step parity `odd`): colours, f* and red fraction.
 // RECOL: some node of the warp has an interface normal (otherwise the
 // recolouring term is zero and the red fraction of every direction is rho_r/rho).
@@ -920,18 +954,8 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
   if (!FUSED && !active) return;
 
   if (active) {
-    R gphi[3] = {R(0), R(0), R(0)}, grho[3] = {R(0), R(0), R(0)};
-    const int lx = threadIdx.x + 1, ly = threadIdx.y + 1, lz = threadIdx.z + 1;
-#pragma unroll
-    for (int t = 0; t < 27; ++t) {
-      if (t == REST) continue;
-      const DT v = tile[(lx + cx_of(t)) + TX * ((ly + cy_of(t)) + TY * (lz + cz_of(t)))];
-      const R w3 = R(3.0 * weight_of(t));
-      const R a = w3 * (R)v.y, b = w3 * (R)v.x;
-      if (cx_of(t) != 0) { gphi[0] += R(cx_of(t)) * a; grho[0] += R(cx_of(t)) * b; }
-      if (cy_of(t) != 0) { gphi[1] += R(cy_of(t)) * a; grho[1] += R(cy_of(t)) * b; }
-      if (cz_of(t) != 0) { gphi[2] += R(cz_of(t)) * a; grho[2] += R(cz_of(t)) * b; }
-    }
+    R gphi[3], grho[3];
+    tile_gradients<R>(tile, threadIdx.x + 1, threadIdx.y + 1, threadIdx.z + 1, gphi, grho);
 
     R f[27];
     Recol<R> rc;
@@ -1127,18 +1151,8 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
       for (int t = 0; t < 27; ++t)
         Store::decode(ps[t * NTHREADS + tid], K.refB[speed2_of(t)], speed2_of(t) == 0 ? K.dref[0] : 0.0f, fr[t],
                       ft[t]);
-      float gphi[3] = {0.f, 0.f, 0.f}, grho[3] = {0.f, 0.f, 0.f};
-      const int lx = threadIdx.x + 1, ly = threadIdx.y + 1, lz = threadIdx.z + 1;
-#pragma unroll
-      for (int t = 0; t < 27; ++t) {
-        if (t == REST) continue;
-        const float2 v = ts[(lx + cx_of(t)) + TX * ((ly + cy_of(t)) + TY * (lz + cz_of(t)))];
-        const float w3 = float(3.0 * weight_of(t));
-        const float a = w3 * v.y, b = w3 * v.x;
-        if (cx_of(t) != 0) { gphi[0] += float(cx_of(t)) * a; grho[0] += float(cx_of(t)) * b; }
-        if (cy_of(t) != 0) { gphi[1] += float(cy_of(t)) * a; grho[1] += float(cy_of(t)) * b; }
-        if (cz_of(t) != 0) { gphi[2] += float(cz_of(t)) * a; grho[2] += float(cz_of(t)) * b; }
-      }
+      float gphi[3], grho[3];
+      tile_gradients<float>(ts, threadIdx.x + 1, threadIdx.y + 1, threadIdx.z + 1, gphi, grho);
       float f[27];
       Recol<float> rc;
       if (is_inlet(G, x, y, z)) {
