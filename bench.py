@@ -43,7 +43,7 @@ import lbm_inputs as L  # noqa: E402
 
 METRIC = "D3Q27 color-fluid MLUPS & % HBM roofline, mixed vs FP32 at stated error"
 UNIT = "MLUPS"
-# algorithmic bytes per node and step of each kernel (see DESIGN.md):
+# algorithmic bytes per node and step of each kernel:
 #   density pass: read 54 populations, write (rho, phi)
 #   collide-stream pass: read (rho, phi) once, read and write 54 populations
 POP_BYTES = {"f64": 8 * 54, "f32": 4 * 54, "f16": 4 * 27, "bf16": 4 * 27}

@@ -3,9 +3,9 @@
  * Saito, Abe & Koyama, "Lattice Boltzmann modeling and simulation of liquid
  * jet breakup" (arXiv 1705.03141), Sec. II, Sec. III and Sec. IV.A.
  *
- * TEST INFRASTRUCTURE ONLY.  This file is the judge of the CUDA path: only
- * the test-suite, the smoke check and the CPU-baseline leg of the benchmark
- * load it.  It shares no code, header or table with the CUDA library.
+ * TEST INFRASTRUCTURE ONLY.  This file is the reference the CUDA path is
+ * checked against: only the test-suite, the smoke check and the CPU-baseline
+ * leg of the benchmark load it.  It shares no code, header or table with the CUDA library.
  *
  * It is written to be checked against the paper by eye, not to be fast:
  *   - dense 27x27 M and M^-1 typed from App. A (the printed matrices),

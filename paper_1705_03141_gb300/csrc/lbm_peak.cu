@@ -9,7 +9,7 @@ namespace {
 
 constexpr int kChains = 8;  // independent FMA chains per thread (hides the FMA latency)
 
-// Every thread runs kChains dependent chains x <- x*a + b for `iters` rounds;
+// Every thread runs kChains dependent chains x <- x*a + b for `iters` iterations;
 // the final values are stored so that nothing is dead code.
 __global__ void __launch_bounds__(256) k_fma_scalar(float* __restrict__ out, int iters, float a, float b) {
   float x[kChains];
@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(256) k_fma_scalar(float* __restrict__ out, int
 }
 
 // The same with Blackwell's packed FP32x2 FMA: kChains/2 float2 chains, the
-// same FLOPs per round.
+// same FLOPs per iteration.
 __global__ void __launch_bounds__(256) k_fma_packed(float* __restrict__ out, int iters, float a, float b) {
   float2 x[kChains / 2];
 #pragma unroll

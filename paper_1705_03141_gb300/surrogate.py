@@ -1,11 +1,11 @@
-"""Jet-trajectory surrogate: train on batched sweeps, judge on held-out simulations.
+"""Jet-trajectory surrogate: train on batched sweeps, check on held-out simulations.
 
 The regime map of Sec. IV.C is drawn from many jet simulations.  This program
 runs regime sweeps (`sweep.run_sweep`: independent jets, one CUDA graph),
 trains the surrogate network (`Mlp`, include/lbm_mlp.h) to map each jet's
 dimensionless groups to its leading-edge trajectory z_LE/D at the sweep's 64
 sample times and to its regime label, and then compares the network's
-answers for held-out jets with their own simulations (the LBM is the judge).
+answers for held-out jets with their own simulations (the LBM decides).
 It also times batch-4096 inference.
 
     python -m paper_1705_03141_gb300.surrogate --train-seeds 2024,2025,2026 --test-seeds 2027,2028,2029,2030
