@@ -93,3 +93,53 @@ def test_null_handles(lib):
     assert lib.lbm_create(8, 8, 8, None, None) == -1
     lib.lbm_free(None)
     assert lib.lbm_time(None) == -1
+    assert lib.lbm_kernel_variant(None) == -1
+    assert lib.lbm_kernels_per_step(None) == -1
+    assert lib.lbm_autotune(None, 4, None) == -1
+    assert lib.lbm_batch_step(None, 1) == -1
+    assert lib.lbm_batch_synchronize(None) == -1
+    lib.lbm_batch_free(None)
+    h = ctypes.c_void_p()
+    assert lib.lbm_batch_create(None, 0, None, ctypes.byref(h)) == -1 and not h.value
+
+
+@pytest.mark.parametrize("storage,variant,ok", [
+    (0, 2, False), (0, 3, False), (0, 4, False),   # FP64: one node per thread only
+    (1, 3, True), (1, 4, False),                   # FP32: fused yes, pipelined (packed only) no
+    (2, 3, True), (2, 4, True), (3, 4, True),      # packed: every variant
+    (1, 5, False), (1, -1, False),
+])
+def test_kernel_variant_validation(lib, storage, variant, ok):
+    w = L.static_droplet(n=8, R=2.0)
+    ps = binding._params_struct(w["params"], storage, variant=variant)
+    n = ctypes.c_size_t()
+    rc = lib.lbm_workspace_size(*w["shape"], ctypes.byref(ps), ctypes.byref(n))
+    assert (rc == 0) == ok
+
+
+def test_two_node_kernel_needs_even_nx(lib):
+    w = L.static_droplet(n=9, R=2.0)
+    ps = binding._params_struct(w["params"], 1, variant=2)
+    n = ctypes.c_size_t()
+    assert lib.lbm_workspace_size(*w["shape"], ctypes.byref(ps), ctypes.byref(n)) == -1
+
+
+def test_fixed_point_range_checked_for_fp32_storages(lib):
+    """The fused pass keeps densities in 2^-22 fixed point: FP32/packed storage rejects rho0 > 64."""
+    w = L.static_droplet(n=8, R=2.0)
+    params = {**w["params"], "rho_r0": 80.0, "rho_b0": 40.0}
+    assert _size(lib, w["shape"], params, 1)[0] == -1
+    assert _size(lib, w["shape"], params, 2)[0] == -1
+    assert _size(lib, w["shape"], params, 0)[0] == 0  # FP64 has no fixed-point pass
+
+
+def test_fused_accumulators_in_workspace(lib):
+    """FP32 and packed storage reserve two 8-byte accumulators per node for the fused pass."""
+    w = L.jet()
+    N = 128 * 128 * 512
+    s64 = _size(lib, w["shape"], w["params"], 0)[1]
+    s32 = _size(lib, w["shape"], w["params"], 1)[1]
+    Ns = 128 * 128 * 514 + (-(128 * 128 * 514) % 64)
+    # FP32: 54 planes x 4 B over Ns storage nodes, pass-1 field 8 B, accumulators 16 B per node
+    assert s32 >= 54 * 4 * Ns + 8 * N + 16 * N
+    assert s64 < 54 * 8 * Ns + 16 * N + 5 * 8 * N + 10 * 2 ** 20  # FP64: no accumulators
