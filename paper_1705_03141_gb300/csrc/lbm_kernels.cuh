@@ -792,7 +792,7 @@ __device__ __forceinline__ void emit(const Store& st, const KConst<R>& K, const 
 }
 
 // FUSED: after each direction (fast rows: each triple of directions), add it to the
-// next step's densities (fused density pass; sacc, io as in k_collide_stream)
+// next step's densities (fused density pass; prow, io as in k_collide_stream)
 template <int T, class Store, typename R, bool FAST, bool RECOL, bool FUSED>
 struct EmitLoop {
   __device__ __forceinline__ static void run(const Store& st, const KConst<R>& K, const Geom& G, const NodeMap& nm,
@@ -868,7 +868,7 @@ __global__ void __launch_bounds__(NTHREADS) k_density(Store st, Geom G,
 // kernel writes t + 1 into counter[(t + 1) & 1] for the next step, so a
 // captured graph of steps needs no parameter updates.  FUSED: (rho, phi) come
 // from the fixed-point accumulators of the previous step, and the kernel
-// accumulates those of the next step (FusedRows, FusedNodes).
+// accumulates those of the next step (fused_row, fused_node).
 template <class Store, int MINB, bool FUSED>
 __global__ void __launch_bounds__(NTHREADS, MINB)
     k_collide_stream(Store st, const __grid_constant__ Geom G,

@@ -72,3 +72,42 @@ def test_fullsize_packed(cuda, reference, storage):
     assert np.max(np.abs(gr - orr)) < tol * scale
     assert np.max(np.abs(gb - orb)) < tol * scale
     assert np.all(np.isfinite(gu))
+
+
+@pytest.mark.parametrize("storage,tol_sym,tol_mass", [("f32", 1e-5, 1e-6), ("f16", 2e-3, 1e-4)])
+def test_large_box_symmetry_and_mass(cuda, storage, tol_sym, tol_mass):
+    """512 x 512 x 1024 nodes (2.7e8: more than 2^31 stored population values in FP32 storage,
+    so every index into them must be 64-bit): a centred droplet at rest in a periodic box keeps
+    its colour masses, stays finite, and stays mirror-symmetric under x <-> y and z -> nz-1-z
+    (a wrong stride or a 32-bit index overflow breaks the symmetry).  Fields stay on the device."""
+    import torch
+
+    nx, ny, nz = 512, 512, 1024
+    w = L.static_droplet()
+    p = dict(w["params"])
+    p["s"] = L.uniform_rates(1.0)
+    dev = torch.device("cuda")
+    x = (torch.arange(nx, device=dev, dtype=torch.float64) - 0.5 * (nx - 1)) ** 2
+    y = (torch.arange(ny, device=dev, dtype=torch.float64) - 0.5 * (ny - 1)) ** 2
+    z = (torch.arange(nz, device=dev, dtype=torch.float64) - 0.5 * (nz - 1)) ** 2
+    d = torch.sqrt(z[:, None, None] + y[None, :, None] + x[None, None, :])
+    acc = 0.5 * (1.0 - torch.tanh(2.0 * (d - 100.0) / 4.0))
+    del d
+    rr = (p["rho_r0"] * acc).contiguous()
+    rb = (p["rho_b0"] * (1.0 - acc)).contiguous()
+    del acc
+    m_r, m_b = float(rr.sum()), float(rb.sum())
+    lat = pkg.Lattice((nx, ny, nz), p, storage=storage)
+    lat.init_fields(rr, rb)
+    lat.step(18)
+    dg = lat.diag()
+    out = (rr, rb, torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev))
+    lat.macro(out)
+    lat.close()
+    assert abs(dg["mass_r"] - m_r) < tol_mass * m_r and abs(dg["mass_b"] - m_b) < tol_mass * m_b
+    for f in out:
+        assert bool(torch.isfinite(f).all())
+    scale = max(p["rho_r0"], p["rho_b0"])
+    for f in (out[0], out[1]):
+        assert float((f - f.transpose(1, 2)).abs().max()) < tol_sym * scale
+        assert float((f - torch.flip(f, dims=[0])).abs().max()) < tol_sym * scale
