@@ -126,7 +126,8 @@ typedef struct {
                             allocates (cudaMalloc) and frees it itself. */
   size_t workspace_bytes;
   int variant;           /* collide-stream kernel: 0 = library's choice (3 for F32
-                            storage, 1 otherwise: the measured faster one),
+                            storage with nx a multiple of 32, 1 otherwise: the
+                            measured faster one),
                             1 = one node per thread, 2 = two x-adjacent nodes per
                             thread with packed FP32x2 arithmetic (needs F32/F16/BF16
                             storage and an even nx), 3 = one node per thread with

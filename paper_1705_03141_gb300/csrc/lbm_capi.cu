@@ -127,7 +127,8 @@ const char* validate(int nx, int ny, int nz, const lbm_params* p) {
 
 Layout plan(int nx, int ny, int nz, const lbm_params* p, const KernelSet* ks, int64_t* Ns_out, int* diag_blocks) {
   const int64_t N = (int64_t)nx * ny * nz;
-  const int64_t Ns = (int64_t)align_up((size_t)nx * ny * (nz + 2), 64);
+  const int64_t nxs = (int64_t)align_up((size_t)nx, 32);  // storage rows: whole 32-node blocks
+  const int64_t Ns = (int64_t)align_up((size_t)nxs * ny * (nz + 2), 64);
   const int64_t Pn = (int64_t)nx * ny;
   int nb = (int)((N + lbmk::DIAG_THREADS - 1) / lbmk::DIAG_THREADS);
   if (nb > 152 * 8) nb = 152 * 8;
@@ -281,17 +282,19 @@ lbm_status lbm_create(int nx, int ny, int nz, const lbm_params* p, lbm** out) {
   int64_t Ns = 0;
   h->L = plan(nx, ny, nz, p, h->ks, &Ns, &h->diag_blocks);
   h->stream = static_cast<cudaStream_t>(p->cuda_stream);
-  // default, as measured on GB300: FP32 storage runs the fused density pass (its
-  // collide-stream kernel is bandwidth-bound, so dropping the separate density pass
-  // pays); the packed storages and FP64 run one node per thread with the two-pass
+  // default, as measured on GB300: FP32 storage runs the fused density pass when rows
+  // fill whole 32-node blocks (its collide-stream kernel is bandwidth-bound, so dropping
+  // the separate density pass pays; partial blocks would take the per-direction atomic
+  // path); the packed storages and FP64 run one node per thread with the two-pass
   // scheme (the packed kernel is issue-bound, and the fused accumulation costs more
   // instructions than the density pass); the two-node kernel's register footprint
   // leaves 8 warps per SM and measured slower everywhere
-  h->variant = p->variant != 0 ? p->variant : (p->storage == LBM_STORE_F32 ? 3 : 1);
+  h->variant = p->variant != 0 ? p->variant : (p->storage == LBM_STORE_F32 && nx % 32 == 0 ? 3 : 1);
   h->fix_ready = false;
 
   Geom& G = h->G;
   G.nx = nx;
+  G.nxs = (int)align_up((size_t)nx, 32);
   G.ny = ny;
   G.nz = nz;
   G.Ns = Ns;

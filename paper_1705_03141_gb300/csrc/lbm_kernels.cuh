@@ -42,7 +42,8 @@ constexpr int NTHREADS = BX * BY * BZ;
 
 struct Geom {
   int nx, ny, nz;
-  int64_t Ns;     // slots per direction plane: nx*ny*(nz+2) rounded up (ghost planes z=-1, z=nz)
+  int nxs;        // storage row length: nx rounded up to a multiple of 32 (whole 32-node blocks per row)
+  int64_t Ns;     // storage nodes: nxs*ny*(nz+2) rounded up (ghost planes z=-1, z=nz)
   int bc[6];
   int inflow;     // inlet disk active on z = 0
   double xc, yc, r2;
@@ -116,7 +117,7 @@ inline KConst<R> make_kconst(const Phys& P) {
 __host__ __device__ __forceinline__ bool is_shear_moment(int j) { return j >= 5 && j <= 9; }  // slots s6, s8
 
 __host__ __device__ __forceinline__ int64_t snode(const Geom& g, int x, int y, int z) {
-  return (int64_t)x + (int64_t)g.nx * ((int64_t)y + (int64_t)g.ny * (int64_t)(z + 1));
+  return (int64_t)x + (int64_t)g.nxs * ((int64_t)y + (int64_t)g.ny * (int64_t)(z + 1));
 }
 __host__ __device__ __forceinline__ int64_t dnode(const Geom& g, int x, int y, int z) {
   return (int64_t)x + (int64_t)g.nx * ((int64_t)y + (int64_t)g.ny * (int64_t)z);
@@ -157,7 +158,7 @@ struct NodeMap {
     base = snode(g, x, y, z);
     const int p[3] = {x, y, z};
     const int n[3] = {g.nx, g.ny, g.nz};
-    const int stride[3] = {1, g.nx, g.nx * g.ny};
+    const int stride[3] = {1, g.nxs, g.nxs * g.ny};
     flip_m = flip_p = bounce_m = bounce_p = 0u;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -197,12 +198,13 @@ struct NodeMap {
 };
 
 // Streaming map of a node on a "fast row": its y and z neighbours are inside the
-// box (a warp is one x-row of a block, so this is warp-uniform), nx is a
-// multiple of 32 and neither x face bounces back.  Then a y/z shift moves whole
-// 32-node storage blocks, and S(x, t) only needs the element index of plane 0
-// of the x-shifted node, e[c_x + 1]; a specular reflection at an x face turns
-// every direction with that c_x into the one two planes away, so it is folded
-// into e as a constant plane shift.
+// box (a warp is one x-row of a block, so this is warp-uniform) and neither x
+// face bounces back.  Storage rows are padded to a multiple of 32 nodes (nxs),
+// so a y/z shift moves whole 32-node storage blocks, and S(x, t) only needs the
+// element index of plane 0 of the x-shifted node, e[c_x + 1]; a specular
+// reflection at an x face turns every direction with that c_x into the one two
+// planes away, so it is folded into e as a constant plane shift.  (Lanes past
+// nx in the last block of a row are idle; their padding slots are never used.)
 struct AoRow {
   int64_t e[3];
   template <int PLANES>
@@ -217,28 +219,14 @@ struct AoRow {
   // element index of plane 0 of the slot S(x, t) (add the plane of t)
   template <int T, int PLANES>
   __device__ __forceinline__ int64_t slot0(const Geom& g) const {
-    return e[cx_of(T) + 1] + (int64_t)((cy_of(T) * g.nx + cz_of(T) * (g.nx * g.ny)) >> 5) * (PLANES * 32);
+    return e[cx_of(T) + 1] + (int64_t)((cy_of(T) * g.nxs + cz_of(T) * (g.nxs * g.ny)) >> 5) * (PLANES * 32);
   }
 };
 
 __device__ __forceinline__ bool fast_row(const Geom& g, int y, int z) {
-  return y > 0 && y < g.ny - 1 && z > 0 && z < g.nz - 1 && (g.nx & 31) == 0 && g.bc[0] != BC_NOSLIP &&
-         g.bc[1] != BC_NOSLIP;
+  return y > 0 && y < g.ny - 1 && z > 0 && z < g.nz - 1 && g.bc[0] != BC_NOSLIP && g.bc[1] != BC_NOSLIP;
 }
 
-__device__ __forceinline__ bool yz_interior(const Geom& g, int y, int z) {
-  return y > 0 && y < g.ny - 1 && z > 0 && z < g.nz - 1;
-}
-
-// node-index offset of c_t (interior nodes: S(x, t) = (x + c_t, t)); strides from the
-// kernel parameters, so the offsets are warp-uniform
-template <int T>
-__device__ __forceinline__ int64_t interior_offset(const Geom& g) {
-  return (int64_t)(cx_of(T) + cy_of(T) * g.nx + cz_of(T) * (g.nx * g.ny));
-}
-__device__ __forceinline__ bool is_interior(const Geom& g, int x, int y, int z) {
-  return x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 && z > 0 && z < g.nz - 1;
-}
 
 // slot holding the post-streaming population (x, t) in a layout (runtime t)
 __device__ __forceinline__ void slot_of(const NodeMap& nm, int layout, int t, int64_t& node, int& dir) {
@@ -889,8 +877,9 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
   if (tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) counter[odd ^ 1] = step + 1;
 
   R fr[27], ft[27];
-  // a warp is one x-row of the block: the fast-row test is warp-uniform
-  const bool fast = fast_row(G, y, z);
+  // a warp is one x-row of the block: the fast-row test is warp-uniform (the fused pass sums
+  // across the 32 lanes of a fast row, so there the row must also be complete in x)
+  const bool fast = fast_row(G, y, z) && (!FUSED || x0 + BX <= G.nx);
   if (FUSED && threadIdx.x == 0) pfast[tid >> 5] = active && fast;
   const int64_t base = snode(G, x, y, z);
   AoRow ar;

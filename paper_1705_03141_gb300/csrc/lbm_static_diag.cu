@@ -119,6 +119,7 @@ extern "C" lbm_status lbm_diag_fields_static(const double* rhoR, const double* r
 
   lbmk::Geom G;
   G.nx = nx;
+  G.nxs = nx;  // the diagnostics read plain fields only
   G.ny = ny;
   G.nz = nz;
   G.Ns = 0;
