@@ -404,17 +404,23 @@ struct DensOf<PlainStore<double>> { using type = double2; using real = double; }
 // load all 27 directions of a node (red and total population) with the layout of the step about to run
 template <class Store, typename R>
 __device__ __forceinline__ void load_node(const Store& st, const KConst<R>& K, const NodeMap& nm, int layout,
-                                          R fr[27], R ft[27]) {
+                                          R& rho_r, R ft[27]) {
   if (layout == 0) {
 #pragma unroll
-    for (int t = 0; t < 27; ++t) st.load(nm.base, t, speed2_of(t), K, fr[t], ft[t]);
+    for (int t = 0; t < 27; ++t) {
+      R fr;
+      st.load(nm.base, t, speed2_of(t), K, fr, ft[t]);
+      rho_r += fr;
+    }
   } else {
 #pragma unroll
     for (int t = 0; t < 27; ++t) {
       int64_t node;
       int dir;
       slot_of(nm, 1, t, node, dir);
-      st.load(node, dir, speed2_of(t), K, fr[t], ft[t]);
+      R fr;
+      st.load(node, dir, speed2_of(t), K, fr, ft[t]);
+      rho_r += fr;
     }
   }
 }
@@ -423,10 +429,14 @@ __device__ __forceinline__ void load_node(const Store& st, const KConst<R>& K, c
 // odd steps the slot S(x, opp(t))
 template <class Store, typename R>
 __device__ __forceinline__ void load_node_fast(const Store& st, const KConst<R>& K, const Geom& G, const AoRow& ar,
-                                               int odd, R fr[27], R ft[27]) {
+                                               int odd, R& rho_r, R ft[27]) {
   if (!odd) {
 #pragma unroll
-    for (int t = 0; t < 27; ++t) st.load_at(ar.e[1], t, speed2_of(t), K, fr[t], ft[t]);
+    for (int t = 0; t < 27; ++t) {
+      R fr;
+      st.load_at(ar.e[1], t, speed2_of(t), K, fr, ft[t]);
+      rho_r += fr;
+    }
   } else {
 #pragma unroll
     for (int t = 0; t < 27; ++t) {
@@ -440,7 +450,9 @@ __device__ __forceinline__ void load_node_fast(const Store& st, const KConst<R>&
         default: e0 = ar.slot0<26, Store::PLANES>(G); break;
 #undef LBMK_CASE
       }
-      st.load_at(e0, opp_of(t), speed2_of(t), K, fr[t], ft[t]);
+      R fr;
+      st.load_at(e0, opp_of(t), speed2_of(t), K, fr, ft[t]);
+      rho_r += fr;
     }
   }
 }
@@ -466,7 +478,8 @@ struct Recol {
   typename MaskOf<R>::type has_n;
 };
 
-// Collision of one node.  fr/ft: post-streaming red and total populations (in).  On return
+// Collision of one node.  rho_r: red density (the sum of the red populations, in
+// direction order); ft: post-streaming total populations (in).  On return
 // f[t] holds f*_t, the total post-collision population including forcing and
 // perturbation, and the returned Recol splits it into colours:
 //   f^r_t = frac f*_t + rc[|c_t|^2] (c_t . n),   f^b_t = f*_t - f^r_t.
@@ -490,14 +503,10 @@ struct Recol {
 // moments 5..27 (mass and momentum of h vanish), R* = R(f) + T^-1(-K m) +
 // closed(F' + Omega^(2)), and f* = V3^-1 R* by one inverse cascade.
 template <typename R>
-__device__ __forceinline__ Recol<R> collide(const KConst<R>& K, const R fr[27], const R ft[27], const R gphi[3],
+__device__ __forceinline__ Recol<R> collide(const KConst<R>& K, const R rho_r, const R ft[27], const R gphi[3],
                                             const R grho[3], R f[27]) {
-  R rho_r = R(0);
 #pragma unroll
-  for (int t = 0; t < 27; ++t) {
-    rho_r += fr[t];
-    f[t] = ft[t];
-  }
+  for (int t = 0; t < 27; ++t) f[t] = ft[t];
   raw_forward(f);  // f holds R(f) from here until raw_inverse
   const R rho = f[0];
   const R rho_b = rho - rho_r;
@@ -818,22 +827,19 @@ __global__ void __launch_bounds__(NTHREADS) k_density(Store st, Geom G,
   const int y = blockIdx.y * BY + threadIdx.y;
   const int z = blockIdx.z * BZ + threadIdx.z;
   if (x >= G.nx || y >= G.ny || z >= G.nz) return;
-  D fr[27], ft[27];
+  D rr = D(0), ft[27];
   if (fast_row(G, y, z)) {
     AoRow ar;
     ar.init<Store::PLANES>(G, x, y, z);
-    load_node_fast(st, K, G, ar, layout, fr, ft);
+    load_node_fast(st, K, G, ar, layout, rr, ft);
   } else {
     NodeMap nm;
     nm.init(G, x, y, z);
-    load_node(st, K, nm, layout, fr, ft);
+    load_node(st, K, nm, layout, rr, ft);
   }
-  D rr = D(0), rt = D(0);
+  D rt = D(0);
 #pragma unroll
-  for (int t = 0; t < 27; ++t) {
-    rr += fr[t];
-    rt += ft[t];
-  }
+  for (int t = 0; t < 27; ++t) rt += ft[t];
   if (!(rt > D(0)) || !(rt < D(1e30))) atomicOr(flag, 1);
   if constexpr (FIX) {
     fix[dnode(G, x, y, z)] = pack_fix((float)rt, (float)rr);
@@ -876,7 +882,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
   const long long step = counter[odd];
   if (tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) counter[odd ^ 1] = step + 1;
 
-  R fr[27], ft[27];
+  R rho_r = R(0), ft[27];
   // a warp is one x-row of the block: the fast-row test is warp-uniform (the fused pass sums
   // across the 32 lanes of a fast row, so there the row must also be complete in x)
   const bool fast = fast_row(G, y, z) && (!FUSED || x0 + BX <= G.nx);
@@ -886,11 +892,11 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
   if (fast) ar.init<Store::PLANES>(G, x, y, z);
   if (active) {
     if (fast) {
-      load_node_fast(st, K, G, ar, odd, fr, ft);
+      load_node_fast(st, K, G, ar, odd, rho_r, ft);
     } else {
       NodeMap nm;
       nm.init(G, x, y, z);
-      load_node(st, K, nm, odd, fr, ft);
+      load_node(st, K, nm, odd, rho_r, ft);
     }
   }
 
@@ -956,7 +962,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
       rc.rho = R(1);
       rc.has_n = false;
     } else {
-      rc = collide(K, fr, ft, gphi, grho, f);
+      rc = collide(K, rho_r, ft, gphi, grho, f);
     }
     if constexpr (FUSED) {
       // the watchdog of pass 1, on the density this step starts from
@@ -1135,11 +1141,13 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
     const int x0 = (tile % ntx) * BX, y0 = ((tile / ntx) % nty) * BY, z0 = (tile / (ntx * nty)) * BZ;
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
     if (x < G.nx && y < G.ny && z < G.nz) {
-      float fr[27], ft[27];
+      float rho_r = 0.0f, ft[27];
 #pragma unroll
-      for (int t = 0; t < 27; ++t)
-        Store::decode(ps[t * NTHREADS + tid], K.refB[speed2_of(t)], speed2_of(t) == 0 ? K.dref[0] : 0.0f, fr[t],
-                      ft[t]);
+      for (int t = 0; t < 27; ++t) {
+        float fr;
+        Store::decode(ps[t * NTHREADS + tid], K.refB[speed2_of(t)], speed2_of(t) == 0 ? K.dref[0] : 0.0f, fr, ft[t]);
+        rho_r += fr;
+      }
       float gphi[3], grho[3];
       tile_gradients<float>(ts, threadIdx.x + 1, threadIdx.y + 1, threadIdx.z + 1, gphi, grho);
       float f[27];
@@ -1152,7 +1160,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
         rc.rho = 1.0f;
         rc.has_n = false;
       } else {
-        rc = collide(K, fr, ft, gphi, grho, f);
+        rc = collide(K, rho_r, ft, gphi, grho, f);
       }
       const bool recol = __any_sync(__activemask(), rc.has_n);
       const bool fast = fast_row(G, y, z);
@@ -1241,12 +1249,14 @@ __global__ void __launch_bounds__(PTHREADS, MINB)
 
   const int64_t base = snode(G, xa, y, z);
   NodeMap m0, m1;
-  F2 fr[27], ft[27];
+  F2 rho_r = F2(0.0f), ft[27];
   if (active) {
     if (!odd) {
 #pragma unroll
       for (int t = 0; t < 27; ++t) {
-        st.load_p(base, t, K.refB[speed2_of(t)].v.x, speed2_of(t) == 0 ? K.dref[0].v.x : 0.0f, fr[t], ft[t]);
+        F2 fr;
+        st.load_p(base, t, K.refB[speed2_of(t)].v.x, speed2_of(t) == 0 ? K.dref[0].v.x : 0.0f, fr, ft[t]);
+        rho_r = rho_r + fr;
       }
     } else {
       m0.init(G, xa, y, z);
@@ -1258,8 +1268,10 @@ __global__ void __launch_bounds__(PTHREADS, MINB)
         slot_of(m0, 1, t, n0, d0);
         slot_of(m1, 1, t, n1, d1);
         const float rB = K.refB[speed2_of(t)].v.x, dR = speed2_of(t) == 0 ? K.dref[0].v.x : 0.0f;
-        st.load_s(n0, d0, rB, dR, fr[t].v.x, ft[t].v.x);
-        st.load_s(n1, d1, rB, dR, fr[t].v.y, ft[t].v.y);
+        F2 fr;
+        st.load_s(n0, d0, rB, dR, fr.v.x, ft[t].v.x);
+        st.load_s(n1, d1, rB, dR, fr.v.y, ft[t].v.y);
+        rho_r = rho_r + fr;
       }
     }
   }
@@ -1303,7 +1315,7 @@ __global__ void __launch_bounds__(PTHREADS, MINB)
   }
 
   F2 f[27];
-  Recol<F2> rc = collide(K, fr, ft, gphi, grho, f);
+  Recol<F2> rc = collide(K, rho_r, ft, gphi, grho, f);
   if (z == 0 && G.inflow) {
     // Dirichlet inlet nodes (Sec. IV.A) replace the collision result lane by lane
 #pragma unroll
