@@ -12,22 +12,25 @@ inline unsigned blocks1(int64_t n, int t) { return (unsigned)((n + t - 1) / t); 
 
 template <class Store>
 struct StoreTraits;
+// minb: resident 256-thread blocks per SM the one-node kernels are compiled for (4: 64 registers,
+// 32 warps; measured faster than 3 once the red populations are summed as they load);
+// minb2: the two-node kernel; minb_pf: the pipelined kernel (68 KB of shared memory per block)
 template <>
 struct StoreTraits<PlainStore<double>> {
   static constexpr bool paired = false;
-  static constexpr int minb = 1, minb2 = 1;
+  static constexpr int minb = 1, minb2 = 1, minb_pf = 1;
   static PlainStore<double> make(void* p, const Geom& G) { return {static_cast<double*>(p), G.Ns}; }
 };
 template <>
 struct StoreTraits<PlainStore<float>> {
   static constexpr bool paired = true;
-  static constexpr int minb = 3, minb2 = 2;
+  static constexpr int minb = 4, minb2 = 2, minb_pf = 3;
   static PlainStore<float> make(void* p, const Geom& G) { return {static_cast<float*>(p), G.Ns}; }
 };
 template <bool B>
 struct StoreTraits<PackedStore<B>> {
   static constexpr bool paired = true;
-  static constexpr int minb = 3, minb2 = 2;
+  static constexpr int minb = 4, minb2 = 2, minb_pf = 3;
   static PackedStore<B> make(void* p, const Geom& G) { return {static_cast<uint32_t*>(p), G.Ns}; }
 };
 
@@ -67,7 +70,7 @@ struct Launch {
       if (variant == 4) {
         static bool attr = false;  // first launch per process: allow the 68 KB of dynamic shared memory
         if (!attr) {
-          cudaError_t e = cudaFuncSetAttribute(k_collide_stream_pf<Store, Tr::minb>,
+          cudaError_t e = cudaFuncSetAttribute(k_collide_stream_pf<Store, Tr::minb_pf>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, PF_SMEM);
           if (e != cudaSuccess) return e;
           attr = true;
@@ -77,8 +80,8 @@ struct Launch {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const dim3 g3 = grid3(G);
         const int ntiles = (int)(g3.x * g3.y * g3.z);
-        const int blocks = ntiles < sms * Tr::minb ? ntiles : sms * Tr::minb;
-        k_collide_stream_pf<Store, Tr::minb><<<blocks, dim3(BX, BY, BZ), PF_SMEM, s>>>(
+        const int blocks = ntiles < sms * Tr::minb_pf ? ntiles : sms * Tr::minb_pf;
+        k_collide_stream_pf<Store, Tr::minb_pf><<<blocks, dim3(BX, BY, BZ), PF_SMEM, s>>>(
             Tr::make(pop, G), G, kc(P), odd, static_cast<const float2*>(dens), counter, (int)g3.x, (int)g3.y, ntiles);
         return cudaGetLastError();
       }
