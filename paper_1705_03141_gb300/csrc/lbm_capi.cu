@@ -141,7 +141,7 @@ Layout plan(int nx, int ny, int nz, const lbm_params* p, const KernelSet* ks, in
   L.fix = o;
   if (ks->has_fused) o = align_up(o + (size_t)4 * N * sizeof(int), 256);
   L.top = o;
-  if (p->bc[5] == LBM_BC_OUTFLOW) o = align_up(o + (size_t)2 * 27 * Pn * ks->real_bytes, 256);
+  if (p->bc[5] == LBM_BC_OUTFLOW) o = align_up(o + (size_t)64 * Pn * ks->real_bytes, 256);
   L.counter = o;
   o = align_up(o + 2 * sizeof(long long), 256);
   L.flag = o;

@@ -1354,53 +1354,59 @@ __device__ __forceinline__ void store_pair(const Store& st, const KConst<R>& K, 
   st.store(node, dir, speed2_of(dir), K, fr, fb, s, q);
 }
 
+// sum over the 32 lanes of a warp, the same value in every lane (butterfly: lanes i and i^o
+// hold the same partial sum at every stage, as addition commutes exactly)
+template <typename R>
+__device__ __forceinline__ R warp_allsum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // convective outflow on the z = nz-1 plane (Sec. IV.A), after the step that
-// produced time t+1; `layout` is the layout of time t+1.
+// produced time t+1; `layout` is the layout of time t+1.  One warp per column
+// (x, y), lane t < 27 for direction t: the plane holds only nx ny nodes, so a
+// thread per node would leave most SMs idle; the lanes reduce rho and the z
+// momentum of the node below with shuffles, then each updates its direction.
 template <class Store>
-__global__ void k_outflow(Store st, Geom G, const __grid_constant__ KConst<typename DensOf<Store>::real> K,
-                          int layout, typename DensOf<Store>::real* __restrict__ top,
-                          unsigned long long* __restrict__ fix) {
+__global__ void __launch_bounds__(256) k_outflow(Store st, Geom G,
+                                                 const __grid_constant__ KConst<typename DensOf<Store>::real> K,
+                                                 int layout, typename DensOf<Store>::real* __restrict__ top,
+                                                 unsigned long long* __restrict__ fix) {
   using R = typename DensOf<Store>::real;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= G.nx || y >= G.ny) return;
   const int64_t Pn = (int64_t)G.nx * G.ny;
-  const int64_t pp = x + (int64_t)G.nx * y;
+  const int64_t pp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;  // warp-uniform
+  if (pp >= Pn) return;
+  const int lane = threadIdx.x & 31;
+  const bool act = lane < 27;
+  const int t = act ? lane : 0;
+  const int x = (int)(pp % G.nx), y = (int)(pp / G.nx);
   NodeMap below, here;
   below.init(G, x, y, G.nz - 2);
   here.init(G, x, y, G.nz - 1);
-  R fr[27], fb[27];
-#pragma unroll
-  for (int t = 0; t < 27; ++t) {
+  R fr = R(0), fb = R(0);
+  if (act) {
     int64_t node;
     int dir;
     slot_of(below, layout, t, node, dir);
-    st.load_rb(node, dir, speed2_of(t), K, fr[t], fb[t]);
+    st.load_rb(node, dir, speed2_of(t), K, fr, fb);
   }
-  R rho = R(0), mz = R(0);
-#pragma unroll
-  for (int t = 0; t < 27; ++t) {
-    const R v = fr[t] + fb[t];
-    rho += v;
-    if (cz_of(t) > 0) mz += v;
-    if (cz_of(t) < 0) mz -= v;
-  }
+  const R v = fr + fb;
+  const R rho = warp_allsum(v);
+  const R mz = warp_allsum(cz_of(t) > 0 && act ? v : cz_of(t) < 0 && act ? -v : R(0));
   R F[3];
   body_force(K, rho, F);
   const R uz = (mz + R(0.5) * F[2]) / rho;
   const R lam = uz > R(0) ? uz : R(0);
   const R inv = R(1) / (R(1) + lam);
-  R sr = R(0), st_ = R(0);
-#pragma unroll
-  for (int t = 0; t < 27; ++t) {
-    R* tr = top + (int64_t)t * Pn + pp;
-    R* tb = top + (int64_t)(27 + t) * Pn + pp;
-    const R nr = (*tr + lam * fr[t]) * inv;
-    const R nb = (*tb + lam * fb[t]) * inv;
+  R nr = R(0), nb = R(0);
+  if (act) {
+    R* tr = top + pp * 64 + t;  // per column: 32 red then 32 blue slots, one line per warp
+    R* tb = tr + 32;
+    nr = (*tr + lam * fr) * inv;
+    nb = (*tb + lam * fb) * inv;
     *tr = nr;
     *tb = nb;
-    sr += nr;
-    st_ += nr + nb;
     int64_t node;
     int dir;
     slot_of(here, layout, t, node, dir);
@@ -1408,7 +1414,8 @@ __global__ void k_outflow(Store st, Geom G, const __grid_constant__ KConst<typen
   }
   // fused density pass: the plane's new populations replace what the collide-stream kernel accumulated
   if (fix) {
-    fix[dnode(G, x, y, G.nz - 1)] = pack_fix((float)st_, (float)sr);
+    const R sr = warp_allsum(nr), sa = warp_allsum(nr + nb);
+    if (lane == 0) fix[dnode(G, x, y, G.nz - 1)] = pack_fix((float)sa, (float)sr);
   }
 }
 
@@ -1492,8 +1499,8 @@ __global__ void k_top_from_state(Store st, Geom G, const __grid_constant__ KCons
     slot_of(nm, layout, t, node, dir);
     R fr, fb;
     st.load_rb(node, dir, speed2_of(t), K, fr, fb);
-    top[(int64_t)t * Pn + pp] = fr;
-    top[(int64_t)(27 + t) * Pn + pp] = fb;
+    top[pp * 64 + t] = fr;  // per column: 32 red then 32 blue slots (27 used)
+    top[pp * 64 + 32 + t] = fb;
   }
 }
 

@@ -100,9 +100,10 @@ struct Launch {
   }
   static cudaError_t outflow(void* pop, const Geom& G, const Phys& P, int layout, void* top, void* fix,
                              cudaStream_t s) {
-    dim3 b(32, 4), g((unsigned)((G.nx + 31) / 32), (unsigned)((G.ny + 3) / 4));
-    k_outflow<Store><<<g, b, 0, s>>>(Tr::make(pop, G), G, kc(P), layout, static_cast<R*>(top),
-                                     static_cast<unsigned long long*>(fix));
+    const int64_t warps = (int64_t)G.nx * G.ny;  // one warp per column of the top plane
+    k_outflow<Store><<<blocks1(warps * 32, 256), 256, 0, s>>>(Tr::make(pop, G), G, kc(P), layout,
+                                                              static_cast<R*>(top),
+                                                              static_cast<unsigned long long*>(fix));
     return cudaGetLastError();
   }
   static cudaError_t init(void* pop, const Geom& G, const Phys& P, const double* rr, const double* rb, const double* u,
