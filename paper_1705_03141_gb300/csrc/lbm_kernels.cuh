@@ -887,11 +887,10 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
   // across the 32 lanes of a fast row, so there the row must also be complete in x)
   const bool fast = fast_row(G, y, z) && (!FUSED || x0 + BX <= G.nx);
   if (FUSED && threadIdx.x == 0) pfast[tid >> 5] = active && fast;
-  const int64_t base = snode(G, x, y, z);
-  AoRow ar;
-  if (fast) ar.init<Store::PLANES>(G, x, y, z);
   if (active) {
     if (fast) {
+      AoRow ar;  // rebuilt for the stores: cheaper than keeping it live through the collision
+      ar.init<Store::PLANES>(G, x, y, z);
       load_node_fast(st, K, G, ar, odd, rho_r, ft);
     } else {
       NodeMap nm;
@@ -971,12 +970,14 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
     // warp-uniform: does any node of the warp carry an interface normal?
     const bool recol = __any_sync(__activemask(), any_(rc.has_n));
     NodeMap nm;
+    AoRow ar;
     if (fast) {
+      ar.init<Store::PLANES>(G, x, y, z);
       if (recol) EmitLoop<0, Store, R, true, true, FUSED>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
       else EmitLoop<0, Store, R, true, false, FUSED>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
     } else {
       if (odd) nm.init(G, x, y, z);
-      else nm.base = base;  // the even step only uses the base
+      else nm.base = snode(G, x, y, z);  // the even step only uses the base
       if (recol) EmitLoop<0, Store, R, false, true, FUSED>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
       else EmitLoop<0, Store, R, false, false, FUSED>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
     }
