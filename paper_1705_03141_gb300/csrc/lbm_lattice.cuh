@@ -15,6 +15,8 @@
 #pragma once
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "lbm_f2.cuh"
 
 namespace lbmk {
@@ -116,10 +118,55 @@ __host__ __device__ __forceinline__ void tri_forward(R& a, R& b, R& c) {
   b = d;
   c = s;
 }
+#if defined(__CUDA_ARCH__)
+// FP32 on the device: the y and z transforms treat the lines at x-index 0 and 2 alike, so
+// those two lines go through one packed FP32x2 transform (a - b as fma(b, -1, a): the
+// same rounding as the subtraction); the values and their rounding are the scalar ones.
+__device__ __forceinline__ void tri_forward2(float& a0, float& a2, float& b0, float& b2, float& c0, float& c2) {
+  const float2 a = make_float2(a0, a2), b = make_float2(b0, b2), c = make_float2(c0, c2);
+  const float2 sum = __fadd2_rn(c, a), d = __ffma2_rn(a, make_float2(-1.f, -1.f), c);
+  const float2 o = __fadd2_rn(sum, b);
+  a0 = o.x;
+  a2 = o.y;
+  b0 = d.x;
+  b2 = d.y;
+  c0 = sum.x;
+  c2 = sum.y;
+}
+__device__ __forceinline__ void tri_inverse2(float& a0, float& a2, float& b0, float& b2, float& c0, float& c2) {
+  const float2 k0 = make_float2(a0, a2), k1 = make_float2(b0, b2), k2 = make_float2(c0, c2);
+  const float2 h2 = __fmul2_rn(make_float2(0.5f, 0.5f), k2);
+  const float2 a = __ffma2_rn(make_float2(-0.5f, -0.5f), k1, h2);
+  const float2 b = __ffma2_rn(k2, make_float2(-1.f, -1.f), k0);
+  const float2 c = __ffma2_rn(make_float2(0.5f, 0.5f), k1, h2);
+  a0 = a.x;
+  a2 = a.y;
+  b0 = b.x;
+  b2 = b.y;
+  c0 = c.x;
+  c2 = c.y;
+}
+#endif
+
 template <typename R>
 __host__ __device__ __forceinline__ void raw_forward(R v[27]) {
 #pragma unroll
   for (int l = 0; l < 9; ++l) tri_forward(v[3 * l + 0], v[3 * l + 1], v[3 * l + 2]);  // x
+#if defined(__CUDA_ARCH__)
+  if constexpr (std::is_same<R, float>::value) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {  // y: lines (x, z) = (0|2, k), then (1, k)
+      tri_forward2(v[9 * k], v[9 * k + 2], v[9 * k + 3], v[9 * k + 5], v[9 * k + 6], v[9 * k + 8]);
+      tri_forward(v[9 * k + 1], v[9 * k + 4], v[9 * k + 7]);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {  // z: lines (x, y) = (0|2, j), then (1, j)
+      tri_forward2(v[3 * j], v[3 * j + 2], v[3 * j + 9], v[3 * j + 11], v[3 * j + 18], v[3 * j + 20]);
+      tri_forward(v[3 * j + 1], v[3 * j + 10], v[3 * j + 19]);
+    }
+    return;
+  }
+#endif
 #pragma unroll
   for (int l = 0; l < 9; ++l) {
     int base = (l % 3) + 9 * (l / 3);
@@ -142,6 +189,23 @@ __host__ __device__ __forceinline__ void tri_inverse(R& a, R& b, R& c) {
 // populations from raw moments: the inverse of raw_forward (z, then y, then x).
 template <typename R>
 __host__ __device__ __forceinline__ void raw_inverse(R v[27]) {
+#if defined(__CUDA_ARCH__)
+  if constexpr (std::is_same<R, float>::value) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {  // z
+      tri_inverse2(v[3 * j], v[3 * j + 2], v[3 * j + 9], v[3 * j + 11], v[3 * j + 18], v[3 * j + 20]);
+      tri_inverse(v[3 * j + 1], v[3 * j + 10], v[3 * j + 19]);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {  // y
+      tri_inverse2(v[9 * k], v[9 * k + 2], v[9 * k + 3], v[9 * k + 5], v[9 * k + 6], v[9 * k + 8]);
+      tri_inverse(v[9 * k + 1], v[9 * k + 4], v[9 * k + 7]);
+    }
+#pragma unroll
+    for (int l = 0; l < 9; ++l) tri_inverse(v[3 * l + 0], v[3 * l + 1], v[3 * l + 2]);  // x
+    return;
+  }
+#endif
 #pragma unroll
   for (int l = 0; l < 9; ++l) tri_inverse(v[l], v[l + 9], v[l + 18]);
 #pragma unroll
