@@ -5,7 +5,8 @@ paper or the mathematics fixes: exact per-colour mass conservation, momentum
 balance, the BGK limit (an independent numpy transcription), the viscosity of
 Eq. (shear) from shear-wave decay, the sound speed of Eq. (press), steady
 Poiseuille flow between halfway bounce-back walls, Laplace's law with
-Eq. (sigma) and the Lamb / Miller-Scriven oscillation period.
+Eq. (sigma), the Lamb / Miller-Scriven oscillation period, and the sign and
+sqrt(g) scaling of the Rayleigh-Taylor growth rate (linear theory).
 """
 import numpy as np
 import pytest
@@ -293,3 +294,66 @@ def test_oscillating_droplet_period():
     assert abs(2 * h1 - T1) / T1 < 0.20
     assert abs(2 * h2 - T2) / T2 < 0.20
     assert (h2 / h1) == pytest.approx(T2 / T1, rel=0.05)
+
+
+def _rt_amplitudes(g, steps, every, nu=None):
+    """Rayleigh-Taylor set-up of Sec. III.C at W = 16 (16 x 16 x 64, heavy fluid over light,
+    walls top and bottom, At = 0.5, A = 0): peak-to-peak height of the phi = 0 surface (linear
+    interpolation per column) every `every` steps, gravity (0, 0, g)."""
+    w = L.rayleigh_taylor(W=16, g=abs(g))
+    p = dict(w["params"])
+    p["g"] = (0.0, 0.0, g)
+    if nu is not None:
+        p["nu_r"] = p["nu_b"] = nu
+    w = {**w, "params": p}
+    rr, rb, u = L.initial_fields(w)
+    o = oracle.Oracle(w["shape"], p)
+    o.init_fields(rr, rb, u)
+
+    def height(r, b):
+        phi = (r - b) / (r + b)  # (z, y, x); light (phi < 0) below the heavy fluid
+        up = (phi[:-1] < 0) & (phi[1:] >= 0)
+        k = np.argmax(up, axis=0)  # first crossing from below in every column
+        lo = np.take_along_axis(phi, k[None], 0)[0]
+        hi = np.take_along_axis(phi, k[None] + 1, 0)[0]
+        h = k - lo / (hi - lo)
+        return float(h.max() - h.min())
+
+    amp = [height(rr, rb)]
+    for _ in range(steps // every):
+        o.step(every)
+        r, b, _ = o.macro()
+        amp.append(height(r, b))
+    return np.array(amp)
+
+
+def test_rayleigh_taylor_sign_of_buoyancy():
+    """Heavy fluid over light grows its interface perturbation under gravity pointing down
+    (-z) and only oscillates (a gravity wave) when gravity points up: pins the sign and the
+    reference density of the buoyancy force of Sec. III.C."""
+    grow = _rt_amplitudes(-1e-4, 600, 100)
+    wave = _rt_amplitudes(+1e-4, 600, 100)
+    assert grow[-1] > 2.0 * grow[0] and np.all(np.diff(grow) > 0)
+    assert np.max(wave[1:]) < 1.05 * wave[0] and np.min(wave) < 0.5 * wave[0]
+
+
+@pytest.mark.slow
+def test_rayleigh_taylor_growth_rate_scales_as_sqrt_g():
+    """Linear Rayleigh-Taylor theory: a mode of wave number k grows at sigma = sqrt(At g k) for
+    a sharp inviscid interface (the textbook limit), less for a diffuse density profile (a
+    factor on At g k that does not depend on g), minus about nu k^2 for viscosity.  At fixed nu
+    the early growth rate must then stay below sqrt(At g k) and scale as sqrt(g):
+    sigma(4 g) / sigma(g) = 2, or 2.09 with the viscous term at nu = 1.25e-3, k = 2 pi / 16."""
+    nu, k, At = 1.25e-3, 2 * np.pi / 16, 0.5
+
+    def rate(g, steps):
+        a = _rt_amplitudes(-g, steps, 50, nu=nu)
+        t = np.arange(len(a)) * 50.0
+        m = (a >= 1.2 * a[0]) & (a <= 2.5 * a[0])  # exponential phase, before the spikes saturate
+        assert m.sum() >= 4
+        return np.polyfit(t[m], np.log(a[m]), 1)[0]
+
+    s1, s4 = rate(5e-5, 1600), rate(2e-4, 800)
+    assert 1.85 < s4 / s1 < 2.35
+    for s, g in ((s1, 5e-5), (s4, 2e-4)):
+        assert 0.3 * np.sqrt(At * g * k) < s < np.sqrt(At * g * k)
