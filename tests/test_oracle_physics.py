@@ -61,6 +61,25 @@ def test_uniform_force_momentum_gain():
     np.testing.assert_allclose(j - m0[2], np.array(g) * o.N * steps, rtol=1e-9, atol=1e-13)
 
 
+def test_dispersed_phase_force_leaves_the_ambient_at_rest():
+    """Sec. IV.A: gravity acts on the dispersed phase's density excess over the ambient density
+    rho_b0, so an ambient fluid at rest feels no force and stays exactly at rest (no hydrostatic
+    gradient is needed), while the buoyancy of Sec. III.C (excess over the mean of the two
+    densities) accelerates the same fluid."""
+    g = (0.0, 0.0, 1e-4)
+    work = L.static_droplet(n=8, R=0.0, rho_r0=1.5)
+    rb = np.full(work["shape"][::-1], work["params"]["rho_b0"])
+    for mode, moves in ((2, False), (1, True)):
+        o = oracle.Oracle(work["shape"], {**work["params"], "force_mode": mode, "g": g})
+        o.init_fields(np.zeros_like(rb), rb)
+        o.step(20)
+        j = np.einsum("id,kizyx->d", C, o.f)
+        if moves:
+            assert abs(j[2]) > 1e-4
+        else:
+            assert np.max(np.abs(j)) == 0.0
+
+
 def _bgk_case():
     p = dict(rho_r0=1.4, rho_b0=1.0, nu_r=0.04, nu_b=0.04, A=0.01, beta=0.7, g=(0.0, 0.0, -1e-4),
              force_mode=1, bc=(0,) * 6, seed=0)
