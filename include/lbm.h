@@ -172,7 +172,10 @@ LBM_EXPORT lbm_status lbm_set_inflow(lbm* h, double xc, double yc, double D, dou
  * collide-perturb-recolour-stream pass (in place, AA pattern) and, with an
  * outflow face, the convective outflow update.  Asynchronous: returns after
  * enqueueing.  Returns LBM_EUNSTABLE if a watchdog flag raised by earlier
- * steps has already been observed by a synchronising call. */
+ * steps has already been observed by a synchronising call.  Runs of 16 steps
+ * replay a captured CUDA graph; with the environment variable LBM_NO_GRAPHS
+ * set (read once per process) every step is launched directly instead (the
+ * same kernels and results, for tools that do not follow graphs). */
 LBM_EXPORT lbm_status lbm_step(lbm* h, int n);
 
 /* Macroscopic fields at the current time: rho_r, rho_b (N each) and
