@@ -12,10 +12,12 @@ gcc on first use and wraps it with ctypes.
 
 Every function is pinned by a ``-m "not gpu"`` test against something other
 than itself (App. A/B identities, conservation laws, the BGK limit, the
-shear-wave decay rate of Eq. (shear), uniform-force momentum gain and the
-Laplace law with Eq. (sigma)).  Parity unpinned: the Rayleigh-Taylor and jet
-set-ups have no printed numbers to compare with (figures only); they are
-covered by the conservation and boundary pins instead.
+shear-wave decay rate of Eq. (shear), uniform-force momentum gain, the
+Laplace law with Eq. (sigma), linear Rayleigh-Taylor growth, and a passive
+colour front carried through the nozzle inlet and the convective outflow).
+Parity unpinned: the Rayleigh-Taylor and jet set-ups have no printed numbers
+to compare with (figures only); they are covered by the conservation,
+boundary and growth-rate pins instead.
 """
 from __future__ import annotations
 

@@ -5,8 +5,10 @@ paper or the mathematics fixes: exact per-colour mass conservation, momentum
 balance, the BGK limit (an independent numpy transcription), the viscosity of
 Eq. (shear) from shear-wave decay, the sound speed of Eq. (press), steady
 Poiseuille flow between halfway bounce-back walls, Laplace's law with
-Eq. (sigma), the Lamb / Miller-Scriven oscillation period, and the sign and
-sqrt(g) scaling of the Rayleigh-Taylor growth rate (linear theory).
+Eq. (sigma), the Lamb / Miller-Scriven oscillation period, the sign and
+sqrt(g) scaling of the Rayleigh-Taylor growth rate (linear theory), and a
+passive colour front carried through the nozzle inlet and the convective
+outflow.
 """
 import numpy as np
 import pytest
@@ -78,6 +80,38 @@ def test_dispersed_phase_force_leaves_the_ambient_at_rest():
             assert abs(j[2]) > 1e-4
         else:
             assert np.max(np.abs(j)) == 0.0
+
+
+def test_inlet_and_convective_outflow_pass_a_colour_front_through():
+    """Sec. IV.A boundaries: a 4 x 4 x 32 column of ambient (blue) fluid flowing up at U, periodic
+    sides, the nozzle inlet covering the whole bottom plane (red at U, f^b = 0) and the convective
+    outflow on top.  With equal densities and no interfacial tension the colour is passive, so
+    the red front must advect at U, the interior must stay exactly uniform (rho = 1, u = U z)
+    while it passes, the blue mass must fall at the advective flux rho_b0 U nx ny, and the blue
+    fluid must leave completely through the outflow.  (The z = 0 inlet layer is overwritten by
+    the collision every step and is left out.)"""
+    nx, ny, nz, U = 4, 4, 32, 0.05
+    p = L._base(rho_r0=1.0, rho_b0=1.0, nu_r=0.02, nu_b=0.02, A=0.0, beta=0.7,
+                bc=(L.PERIODIC, L.PERIODIC, L.PERIODIC, L.PERIODIC, L.INFLOW_WALL, L.OUTFLOW),
+                inflow=dict(xc=1.5, yc=1.5, D=100.0, u_j0=U, noise_frac=0.0))
+    o = oracle.Oracle((nx, ny, nz), p)
+    shape = (nz, ny, nx)
+    u = np.zeros((3,) + shape)
+    u[2] = U
+    o.init_fields(np.zeros(shape), np.ones(shape), u)
+    blue = {}
+    for t in range(100, 1001, 100):
+        o.step(100)
+        r, b, uu = o.macro()
+        assert np.max(np.abs((r + b)[1:] - 1.0)) < 1e-12
+        assert np.max(np.abs(uu[2][1:] - U)) < 1e-12 and np.max(np.abs(uu[:2])) < 1e-12
+        blue[t] = b[1:].sum()
+        if t <= 500:  # the front is inside the box: phi = 0 about U t above the inlet plane
+            phi = ((r - b) / (r + b))[1:].mean(axis=(1, 2))
+            front = 1 + np.argmax(phi < 0)
+            assert abs(front - U * t) < 2.5
+    assert blue[100] - blue[500] == pytest.approx(1.0 * U * nx * ny * 400, rel=1e-3)
+    assert blue[1000] < 1e-3
 
 
 def _bgk_case():
