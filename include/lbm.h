@@ -286,7 +286,8 @@ LBM_EXPORT lbm_status lbm_measure_fp32_peak(void* cuda_stream, int packed, doubl
  * fields rhoR, rhoB (N = nx*ny*nz doubles each, x fastest, e.g. filled by
  * lbm_macro into device buffers) to out[0..3] = {mass_r, mass_b,
  * z_leading_edge, dp_laplace}, defined exactly as in lbm_diag; rho_r0/rho_b0
- * give alpha_r as in lbm_create.
+ * give alpha_r as in lbm_create and must satisfy the same range (density
+ * ratio >= 19/27), else LBM_EINVAL.
  * It exists for callers that cannot allocate device memory: code whose host
  * framework owns every device allocation through its own pool, or loops that
  * forbid cudaMalloc and the synchronisation it implies.  It calls no
@@ -298,10 +299,14 @@ LBM_EXPORT lbm_status lbm_measure_fp32_peak(void* cuda_stream, int packed, doubl
  * call before any stream capture.  All calls share the array and leave their
  * contents in it; every slot a call reads is written by the same call first,
  * so nothing needs clearing, but calls that overlap on the GPU (several
- * streams or host threads at once) race on it.  Work goes on cuda_stream
- * (NULL = legacy default stream); out may be device memory, or host memory,
- * in which case the call synchronises the stream.  *err (may be NULL) receives
- * a static message. */
+ * streams or host threads at once) race on it.  rhoR and rhoB must be device
+ * (or managed) memory of the current device, else LBM_EINVAL; the host cannot
+ * check that they hold N doubles.  Work goes on cuda_stream (NULL = legacy
+ * default stream) of the current device; out may be device memory of that
+ * device, or host memory, in which case the call synchronises the stream: a
+ * host out is refused with LBM_EINVAL while cuda_stream is being captured, so
+ * under capture out must be device memory.  *err (may be NULL) receives a
+ * static message. */
 LBM_EXPORT lbm_status lbm_diag_fields_static(const double* rhoR, const double* rhoB, int nx, int ny, int nz,
                                              double rho_r0, double rho_b0, double* out, void* cuda_stream,
                                              const char** err);

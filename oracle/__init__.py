@@ -48,6 +48,7 @@ class OrcParams(ctypes.Structure):
         ("u_j0", ctypes.c_double), ("noise_frac", ctypes.c_double),
         ("seed", ctypes.c_uint64),
         ("perturb_literal", ctypes.c_int),
+        ("ghost_mode", ctypes.c_int),
     ]
 
 
@@ -115,6 +116,7 @@ def make_params(p: dict) -> OrcParams:
         o.u_j0, o.noise_frac = inl["u_j0"], inl.get("noise_frac", 0.0)
     o.seed = p.get("seed", 0)
     o.perturb_literal = int(p.get("perturb_literal", 0))
+    o.ghost_mode = int(p.get("ghost_mode", 0))
     return o
 
 

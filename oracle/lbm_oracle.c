@@ -169,6 +169,8 @@ typedef struct {
   double xc, yc, D, u_j0, noise_frac;
   uint64_t seed;
   int perturb_literal;     /* 1: Eq. (perturb) exactly as printed (no square) */
+  int ghost_mode;          /* gradient ghost next to a wall: 0 mirror (R10); 1 periodic wrap and
+                              2 mirror about the wall node are planted mistakes for the tests */
 } orc_params;
 
 /* alpha_b = 8/27 (Sec. II); Grunau relation gamma = (1-alpha_b)/(1-alpha_r). */
@@ -261,10 +263,20 @@ static int is_inlet(const orc_params* p, const dims* d, int x, int y, int z) {
   return dx * dx + dy * dy < 0.25 * p->D * p->D;
 }
 
-/* neighbour used by the gradient stencil: periodic wrap, otherwise clamp (R10) */
-static int nb_coord(int q, int n, int bc_lo, int bc_hi) {
-  if (q < 0) return bc_lo == BC_PERIODIC ? q + n : 0;
-  if (q >= n) return bc_hi == BC_PERIODIC ? q - n : n - 1;
+/* neighbour used by the gradient stencil: periodic wrap, otherwise the mirror ghost of R10
+ * (the index is clamped into the box: the ghost one link outside a wall carries the value of
+ * the wall node, a mirror about the half-link plane where the walls reflect).  ghost_mode 1
+ * and 2 are deliberately wrong readings (wrap across a wall; mirror about the wall node) that
+ * only the tests select, to show that the wall-symmetry pin detects them. */
+static int nb_coord(int q, int n, int bc_lo, int bc_hi, int ghost_mode) {
+  if (q < 0) {
+    if (bc_lo == BC_PERIODIC || ghost_mode == 1) return q + n;
+    return ghost_mode == 2 ? -q : 0;
+  }
+  if (q >= n) {
+    if (bc_hi == BC_PERIODIC || ghost_mode == 1) return q - n;
+    return ghost_mode == 2 ? 2 * (n - 1) - q : n - 1;
+  }
   return q;
 }
 
@@ -331,9 +343,9 @@ static void node_update(const orc_params* p, const dims* d, const double* f, con
   /* isotropic central gradients of phi, rho_r, rho_b (Sec. II, gradient scheme) */
   double gphi[3] = {0, 0, 0}, grr[3] = {0, 0, 0}, grb[3] = {0, 0, 0};
   for (int i = 1; i < Q; ++i) {
-    int xx = nb_coord(x + C[i][0], d->nx, p->bc[0], p->bc[1]);
-    int yy = nb_coord(y + C[i][1], d->ny, p->bc[2], p->bc[3]);
-    int zz = nb_coord(z + C[i][2], d->nz, p->bc[4], p->bc[5]);
+    int xx = nb_coord(x + C[i][0], d->nx, p->bc[0], p->bc[1], p->ghost_mode);
+    int yy = nb_coord(y + C[i][1], d->ny, p->bc[2], p->bc[3], p->ghost_mode);
+    int zz = nb_coord(z + C[i][2], d->nz, p->bc[4], p->bc[5], p->ghost_mode);
     int64_t m = lin(d, xx, yy, zz);
     double r = fl->rr[m], b = fl->rb[m];
     double ph = (r - b) / (r + b);

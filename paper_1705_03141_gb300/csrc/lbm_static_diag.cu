@@ -75,13 +75,25 @@ lbm_status scratch_for_current_device(double** out, const char** why) {
   return LBM_OK;
 }
 
-bool on_device(const void* ptr) {
+// device memory of the current device, or managed memory (reachable from every device)
+bool on_device(const void* ptr, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
+// host memory the runtime knows (pinned, registered) or plain pageable memory
+bool on_host(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
 }
 
 }  // namespace
@@ -109,9 +121,39 @@ extern "C" lbm_status lbm_diag_fields_static(const double* rhoR, const double* r
     *why = "rho_r0 and rho_b0 must be > 0";
     return LBM_EINVAL;
   }
-  if (!on_device(rhoR) || !on_device(rhoB)) {
-    *why = "rhoR and rhoB must be device pointers";
+  const double alpha_b = 8.0 / 27.0;
+  const double alpha_r = 1.0 - (1.0 - alpha_b) / (rho_r0 / rho_b0);  // gamma = (1-alpha_b)/(1-alpha_r)
+  if (!(alpha_r >= 0.0 && alpha_r < 1.0)) {  // the range lbm_create accepts
+    *why = "density ratio rho_r0/rho_b0 must be >= 19/27 (alpha_r in [0,1))";
     return LBM_EINVAL;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    *why = "no usable current CUDA device";
+    return LBM_ECUDA;
+  }
+  if (!on_device(rhoR, dev) || !on_device(rhoB, dev)) {
+    *why = "rhoR and rhoB must be device memory of the current device";
+    return LBM_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const bool out_dev = !on_host(out);
+  if (out_dev && !on_device(out, dev)) {
+    *why = "out must be host memory or device memory of the current device";
+    return LBM_EINVAL;
+  }
+  if (!out_dev) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+      cudaGetLastError();
+      *why = "cudaStreamIsCapturing failed on cuda_stream";
+      return LBM_ECUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone) {
+      *why = "out must be device memory while cuda_stream is being captured (a host result needs a synchronisation)";
+      return LBM_EINVAL;
+    }
   }
   double* scratch = nullptr;
   lbm_status st = scratch_for_current_device(&scratch, why);
@@ -126,13 +168,9 @@ extern "C" lbm_status lbm_diag_fields_static(const double* rhoR, const double* r
   for (int f = 0; f < 6; ++f) G.bc[f] = 0;
   G.inflow = 0;
   G.xc = G.yc = G.r2 = 0.0;
-  const double alpha_b = 8.0 / 27.0;
-  const double alpha_r = 1.0 - (1.0 - alpha_b) / (rho_r0 / rho_b0);
   const int nblocks = (int)((N + lbmk::DIAG_THREADS - 1) / lbmk::DIAG_THREADS);
-  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   double* partial = scratch;
   double* result = scratch + (long long)kStaticBlocks * lbmk::DIAG_VALS;
-  const bool out_dev = on_device(out);
 
   lbmk::k_diag_partial<<<nblocks, lbmk::DIAG_THREADS, 0, s>>>(G, alpha_r, alpha_b, rhoR, rhoB, partial);
   k_diag_final_static<<<1, 32 * lbmk::DIAG_VALS, 0, s>>>(nblocks, partial, out_dev ? out : result);

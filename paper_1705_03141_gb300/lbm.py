@@ -153,19 +153,33 @@ def measure_fp32_peak(packed=False, stream=None):
 
 
 def diag_fields_static(rho_r, rho_b, rho_r0, rho_b0, out=None, stream=None):
-    """Allocation-free FP64 diagnostics of device fields rho_r, rho_b (torch float64 CUDA tensors,
-    shape (nz, ny, nx)): (mass_r, mass_b, z_leading_edge, dp_laplace).  Its scratch is a static
-    device array inside the library; see lbm_diag_fields_static in include/lbm.h."""
+    """Allocation-free FP64 diagnostics of device fields rho_r, rho_b (torch float64 CUDA tensors of
+    one shape (nz, ny, nx), on one device): (mass_r, mass_b, z_leading_edge, dp_laplace).  The call
+    runs with the fields' device current, on that device's current stream unless `stream` is given;
+    `out` is None (a host result) or a float64 tensor of at least 4 elements on the same device.
+    Its scratch is a static device array inside the library; see lbm_diag_fields_static in
+    include/lbm.h."""
     import torch
 
+    if not (isinstance(rho_r, torch.Tensor) and isinstance(rho_b, torch.Tensor)):
+        raise TypeError("rho_r and rho_b must be torch tensors")
+    if rho_r.dim() != 3 or rho_b.shape != rho_r.shape:
+        raise ValueError(f"rho_r and rho_b must have one 3-D shape (nz, ny, nx), got {tuple(rho_r.shape)} "
+                         f"and {tuple(rho_b.shape)}")
+    if not rho_r.is_cuda or rho_b.device != rho_r.device:
+        raise ValueError("rho_r and rho_b must live on one CUDA device")
     nz, ny, nx = rho_r.shape
     host = out is None
     if host:
         out = np.zeros(4)
-    st = torch.cuda.current_stream() if stream is None else stream
+    elif not (isinstance(out, torch.Tensor) and out.device == rho_r.device and out.dtype == torch.float64
+              and out.is_contiguous() and out.numel() >= 4):
+        raise ValueError("out must be a contiguous float64 tensor of >= 4 elements on the fields' device")
     msg = ctypes.c_char_p()
-    rc = library().lbm_diag_fields_static(_ptr(rho_r), _ptr(rho_b), int(nx), int(ny), int(nz), float(rho_r0),
-                                          float(rho_b0), _ptr(out), st.cuda_stream, ctypes.byref(msg))
+    with torch.cuda.device(rho_r.device):
+        st = torch.cuda.current_stream(rho_r.device) if stream is None else stream
+        rc = library().lbm_diag_fields_static(_ptr(rho_r), _ptr(rho_b), int(nx), int(ny), int(nz), float(rho_r0),
+                                              float(rho_b0), _ptr(out), st.cuda_stream, ctypes.byref(msg))
     if rc != 0:
         raise LbmError(rc, (msg.value or b"").decode())
     return out

@@ -88,8 +88,23 @@ def test_packed_storage_error_budget(cuda, name, storage, variant):
     scale = max(np.max(np.abs(orr)), np.max(np.abs(orb)))
     assert np.max(np.abs(gr - orr)) < tol * scale
     assert np.max(np.abs(gb - orb)) < tol * scale
-    assert np.all(np.isfinite(gu))
+    _check_packed_velocity(gu, ou, storage, f"{name} {storage} variant {variant}")
     lat.close()
+
+
+def _check_packed_velocity(gu, ou, storage, what):
+    """Velocity of packed storage, element by element against the oracle.  The stored deviation
+    of a population from its rest value is, in these flows, itself O(|u| rho w_i), so its
+    rounding (2^-11 half, 2^-8 bfloat16, relative) perturbs u by a fixed fraction of |u| per
+    store, not of rho; the red fraction's 2^-17 enters u only through the recolouring.  Bound:
+    the measured error after 100 steps with a margin (half 1.5 %, bfloat16 12 % of max|u|); a
+    decoding slip that keeps the densities (e.g. two directions of one speed class swapped)
+    moves u by O(max|u|)."""
+    assert np.all(np.isfinite(gu))
+    umax = float(np.max(np.abs(ou)))
+    err = float(np.max(np.abs(gu - ou)))
+    print(f"packed velocity {what}: max|du| = {err:.3e}, max|u| = {umax:.3e}, ratio {err / umax:.3e}")
+    assert err < (0.015 if storage == "f16" else 0.12) * umax
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])

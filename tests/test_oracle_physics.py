@@ -317,9 +317,11 @@ def _lamb_period(R, sigma, rho1, rho2, nu):
     return 2 * np.pi / w
 
 
-def _half_period(A, steps):
+def _half_period(A, steps, rho_r0=1.0, rho_b0=1.0):
+    """First maximum-to-minimum half period of the major semi-axis of a prolate drop (32^3,
+    axes 10/8/8, nu = 0.01), and the Miller-Scriven period for its equivalent radius."""
     n, axes, nu = 32, (10.0, 8.0, 8.0), 0.01
-    work = L.oscillating_droplet(n=n, axes=axes, nu=nu, A=A)
+    work = L.oscillating_droplet(n=n, axes=axes, nu=nu, A=A, rho_r0=rho_r0, rho_b0=rho_b0)
     rr, rb, u = L.initial_fields(work)
     o = oracle.Oracle(work["shape"], work["params"])
     o.init_fields(rr, rb, u)
@@ -342,20 +344,29 @@ def _half_period(A, steps):
         return ts[i] + 10 * 0.5 * (y0 - y2) / (y0 - 2 * y1 + y2)
 
     sigma = 4 / 9 * A * (3 * nu + 0.5)
-    return vertex(i_min) - vertex(max(i_max, 1)), _lamb_period((10 * 8 * 8) ** (1 / 3), sigma, 1.0, 1.0, nu)
+    T = _lamb_period((10 * 8 * 8) ** (1 / 3), sigma, rho_r0, rho_b0, nu)
+    return vertex(i_min) - vertex(max(i_max, 1)), T
 
 
 @pytest.mark.slow
 def test_oscillating_droplet_period():
     """Eqs. (resoFreq)-(Lamb): the n = 2 period of a slightly prolate drop (32^3, axes 10/8/8,
-    nu = 0.01, gamma = 1).  At this small radius (R_e = 8.6, interface width 4 ~ R/2, periodic
-    box 32) the measured period runs 12-17 % long, so we require 20 % on the period and 5 % on
-    the ratio of the periods at A and A/2, which cancels most of the finite-size error."""
+    nu = 0.01).  At this small radius (R_e = 8.6, interface width 4 ~ R/2, periodic box 32)
+    the measured period runs 12-17 % long (the same excess, 14-17 %, appears at the paper's own
+    41^3 set-up of Table II; it falls as the box and the drop grow), so the absolute period is
+    held to 25 % (measured 14 % at gamma = 1, 19.5 % at gamma = 4), and the two ratios that
+    cancel most of the finite-size error are held tighter: the periods at A and A/2 (surface
+    tension, Eq. sigma) to 5 %, and the periods at density ratio gamma = 1 and gamma = 4 (the
+    drop's inertia against the ambient's, (n+1) rho_1 + n rho_2 in Eq. Lamb; Lamb's ratio
+    1.274) to 7 % (measured 4.2 % here, 2.4 % at 41^3): an inertia that ignored the density
+    ratio would give 1.0, 21 % off."""
     h1, T1 = _half_period(0.01, 1300)
     h2, T2 = _half_period(0.005, 1700)
-    assert abs(2 * h1 - T1) / T1 < 0.20
-    assert abs(2 * h2 - T2) / T2 < 0.20
+    h4, T4 = _half_period(0.01, 1200, rho_r0=1.0, rho_b0=0.25)
+    for h, T in ((h1, T1), (h2, T2), (h4, T4)):
+        assert abs(2 * h - T) / T < 0.25
     assert (h2 / h1) == pytest.approx(T2 / T1, rel=0.05)
+    assert (h1 / h4) == pytest.approx(T1 / T4, rel=0.07)
 
 
 def _rt_amplitudes(g, steps, every, nu=None):
@@ -419,3 +430,55 @@ def test_rayleigh_taylor_growth_rate_scales_as_sqrt_g():
     assert 1.85 < s4 / s1 < 2.35
     for s, g in ((s1, 5e-5), (s4, 2e-4)):
         assert 0.3 * np.sqrt(At * g * k) < s < np.sqrt(At * g * k)
+
+
+def _mirror_pair(ghost_mode=0, steps=60):
+    """A red cap on a free-slip wall against the same cap mirrored in a periodic box.
+
+    Half box (16, 8, 16): x and z periodic, free-slip walls on both y faces.  Full box
+    (16, 16, 16), periodic everywhere, holding the half-box fields in its upper half y + 8 and
+    their mirror image Y -> 15 - Y in its lower half (u_y reversed).  Specular reflection at a
+    wall halfway between nodes (R13) and the mirror ghost of the gradient stencil (R10) make
+    the wall a symmetry plane, so the two runs must agree node by node."""
+    nx, ny, nz = 16, 8, 16
+    p = L._base(rho_r0=1.5, rho_b0=1.0, nu_r=0.02, nu_b=0.01, A=0.01, beta=0.7, force_mode=3,
+                g=(2e-5, 0.0, -1e-5))
+    full = dict(shape=(nx, 2 * ny, nz), params={**p, "bc": (L.PERIODIC,) * 6})
+    x, y, z = L._grid(full["shape"])
+    d = np.sqrt((x - 6.0) ** 2 + (y - (ny - 0.5)) ** 2 + (z - 9.0) ** 2)
+    t = np.tanh(2.0 * (d - 5.0) / 4.0)
+    rr, rb = 0.75 * (1.0 - t), 0.5 * (1.0 + t)
+    rng = np.random.default_rng(11)
+    u = np.zeros((3,) + rr.shape)
+    for c in range(3):
+        k = rng.integers(1, 3, 3)
+        u[c] = 0.02 * np.sin(2 * np.pi * k[0] * x / nx + rng.uniform(0, 6)) * np.cos(
+            2 * np.pi * k[1] * y / (2 * ny) + rng.uniform(0, 6)) * np.sin(2 * np.pi * k[2] * z / nz + rng.uniform(0, 6))
+    mir = lambda a: a[:, ::-1, :]  # noqa: E731  (z, y, x): Y -> 2 ny - 1 - Y
+    rr, rb = 0.5 * (rr + mir(rr)), 0.5 * (rb + mir(rb))
+    u = np.stack([0.5 * (u[0] + mir(u[0])), 0.5 * (u[1] - mir(u[1])), 0.5 * (u[2] + mir(u[2]))])
+    of = oracle.Oracle(full["shape"], full["params"])
+    of.init_fields(rr, rb, u)
+    of.step(steps)
+    half_bc = (L.PERIODIC, L.PERIODIC, L.FREESLIP, L.FREESLIP, L.PERIODIC, L.PERIODIC)
+    oh = oracle.Oracle((nx, ny, nz), {**p, "bc": half_bc, "ghost_mode": ghost_mode})
+    oh.init_fields(np.ascontiguousarray(rr[:, ny:]), np.ascontiguousarray(rb[:, ny:]),
+                   np.ascontiguousarray(u[:, :, ny:]))
+    oh.step(steps)
+    (fr, fb, fu), (hr, hb, hu) = of.macro(), oh.macro()
+    err_rho = max(np.abs(hr - fr[:, ny:]).max(), np.abs(hb - fb[:, ny:]).max())
+    err_u = np.abs(hu - fu[:, :, ny:]).max()
+    return err_rho, err_u, np.abs(fu).max()
+
+
+def test_free_slip_wall_is_a_mirror_plane():
+    """R10 and R13 pinned by symmetry: with the mirror ghost, a drop sitting on a free-slip wall
+    evolves exactly like the mirrored drop in a periodic box of twice the width (FP64 round-off
+    after 60 steps), while the two plausible misreadings of the gradient ghost planted in the
+    oracle (a periodic wrap across the wall; a mirror about the wall node instead of the
+    half-link) depart from it by orders of magnitude more."""
+    e_rho, e_u, umax = _mirror_pair(0)
+    assert e_rho < 1e-12 and e_u < 1e-12 * max(umax, 1.0)
+    for planted in (1, 2):
+        p_rho, p_u, _ = _mirror_pair(planted)
+        assert p_rho > 1e-6 or p_u > 1e-7, f"ghost_mode {planted} not detected"

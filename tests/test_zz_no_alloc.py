@@ -71,3 +71,60 @@ def test_static_diag_rejects_oversized_boxes(cuda):
                                               out.ctypes.data, None, ctypes.byref(msg))
     assert rc == -1
     assert b"too large" in msg.value
+
+
+def test_static_diag_refuses_bad_arguments_on_the_host(cuda):
+    """Mismatched shapes, host fields, a density ratio lbm_create would refuse, and a host result
+    requested while the stream is being captured are all refused before any launch."""
+    import ctypes
+
+    import torch
+
+    w = L.static_droplet(n=8, R=2.5)
+    rr, rb, _ = L.initial_fields(w)
+    r = torch.from_numpy(rr).cuda()
+    b = torch.from_numpy(rb).cuda()
+    good = pkg.diag_fields_static(r, b, 1.0, 1.0)  # also the one-time set-up, before any capture
+    assert good[0] == pytest.approx(rr.sum(), rel=1e-13)
+    with pytest.raises(ValueError):
+        pkg.diag_fields_static(r, b[:-1], 1.0, 1.0)
+    with pytest.raises(ValueError):
+        pkg.diag_fields_static(r, b, 1.0, 1.0, out=torch.zeros(3, dtype=torch.float64, device=r.device))
+    lib = pkg.library()
+    msg = ctypes.c_char_p()
+    out = np.zeros(4)
+    host = np.ascontiguousarray(rb)
+    rc = lib.lbm_diag_fields_static(host.ctypes.data, b.data_ptr(), 8, 8, 8, 1.0, 1.0, out.ctypes.data, None,
+                                    ctypes.byref(msg))
+    assert rc == -1 and b"device memory" in msg.value
+    rc = lib.lbm_diag_fields_static(r.data_ptr(), b.data_ptr(), 8, 8, 8, 0.5, 1.0, out.ctypes.data, None,
+                                    ctypes.byref(msg))
+    assert rc == -1 and b"19/27" in msg.value
+    # under capture a host result would need a synchronisation: refused, the capture stays valid
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    x = torch.zeros(4, dtype=torch.float64, device=r.device)
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side, capture_error_mode="thread_local"):
+            rc = lib.lbm_diag_fields_static(r.data_ptr(), b.data_ptr(), 8, 8, 8, 1.0, 1.0, out.ctypes.data,
+                                            side.cuda_stream, ctypes.byref(msg))
+            x.add_(1.0)
+    assert rc == -1 and b"captured" in msg.value
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(x[0]) == 1.0  # one replay of the captured add
+
+
+@pytest.mark.skipif("__import__('torch').cuda.device_count() < 2")
+def test_static_diag_refuses_fields_of_another_device(cuda):
+    import ctypes
+
+    import torch
+
+    r = torch.ones(8, dtype=torch.float64, device="cuda:1")
+    msg = ctypes.c_char_p()
+    out = np.zeros(4)
+    with torch.cuda.device(0):
+        rc = pkg.library().lbm_diag_fields_static(r.data_ptr(), r.data_ptr(), 2, 2, 2, 1.0, 1.0, out.ctypes.data,
+                                                  None, ctypes.byref(msg))
+    assert rc == -1 and b"current device" in msg.value
