@@ -77,6 +77,12 @@ typedef enum {
  *  INFLOW_WALL a free-slip wall whose plane carries the circular inlet set by
  *              lbm_set_inflow(); only allowed on -z.
  *  OUTFLOW     convective outflow of Sec. IV.A; only allowed on +z.
+ *  HALO        the z face joins the box to a neighbouring z-slab of a larger
+ *              domain held by another handle (spatial decomposition along z,
+ *              possibly on another GPU or process); only allowed on -z / +z.
+ *              Populations crossing the face and the densities the gradient
+ *              stencil reads across it come from the neighbour through the
+ *              halo exchange below; such a handle steps with lbm_step_pass.
  * Gradients next to a non-periodic face use a mirror ghost value (zero
  * normal gradient). */
 typedef enum {
@@ -84,7 +90,8 @@ typedef enum {
   LBM_BC_NOSLIP = 1,
   LBM_BC_FREESLIP = 2,
   LBM_BC_INFLOW_WALL = 3,
-  LBM_BC_OUTFLOW = 4
+  LBM_BC_OUTFLOW = 4,
+  LBM_BC_HALO = 5
 } lbm_bc;
 
 /* Body force F(x, t) used in Eq. (Momentum) and Eq. (ketFd).
@@ -310,6 +317,58 @@ LBM_EXPORT lbm_status lbm_measure_fp32_peak(void* cuda_stream, int packed, doubl
 LBM_EXPORT lbm_status lbm_diag_fields_static(const double* rhoR, const double* rhoB, int nx, int ny, int nz,
                                              double rho_r0, double rho_b0, double* out, void* cuda_stream,
                                              const char** err);
+
+/* ---- Spatial decomposition along z (z-slabs) -------------------------
+ * A domain of nx x ny x NZ nodes can be split into slabs nx x ny x nz_k, one
+ * handle each (same nx, ny, storage and parameters; faces between slabs are
+ * LBM_BC_HALO, the outer z faces keep the domain's conditions, or are HALO
+ * both ways round for a domain periodic in z).  The split run computes
+ * exactly the single-domain update (Eq. LBE with the collision of Sec. II is
+ * local except for the 26-neighbour gradient stencil and the streaming to
+ * neighbours, both one node deep): each node gets the same inputs, so FP64
+ * and FP32 results are bitwise those of one handle over the whole domain.
+ *
+ * Slab handles do not accept lbm_step, lbm_profile_step, lbm_autotune or a
+ * batch (LBM_ESTATE); they use the fused-density variant 3 nowhere (the
+ * default becomes 1; asking for 3 gives LBM_EINVAL).  One time step of the
+ * decomposed domain, with the exchange of a phase meaning: for every pair of
+ * adjacent slabs (lower L, upper U), pack(L, +z) -> unpack(U, -z) and
+ * pack(U, -z) -> unpack(L, +z) through a buffer of lbm_halo_bytes:
+ *     lbm_step_pass(h, 1) on every slab        (density / phase field)
+ *     exchange LBM_HALO_DENS                   (the (rho, phi) planes next to each face)
+ *     lbm_step_pass(h, 2) on every slab        (collide-stream (+ outflow); t advances)
+ *     exchange LBM_HALO_POP_IN  if the step just taken was even (t now odd)
+ *     exchange LBM_HALO_POP_OUT if it was odd (t now even)
+ * With the in-place AA pattern an even step writes only a node's own slots,
+ * and the odd step that follows reads and writes the slots of its
+ * neighbours: POP_IN hands each slab a copy of the slots its odd step reads
+ * across a face (those of the neighbour's boundary plane holding the
+ * populations that move across the face, 9 directions per colour, into
+ * this slab's ghost plane), and POP_OUT returns what the odd step wrote into
+ * the ghost plane to the neighbour's boundary plane.  After each step the slabs' states are complete: fields,
+ * populations and diagnostics of each slab are those of its part of the
+ * domain (lbm_diag's leading edge and pressure means are per slab).
+ *
+ * Buffers are device memory of the handle's device (for another device or
+ * process, copy them there: a plain byte buffer).  Pack and unpack are
+ * stream-ordered copies on the handle's stream; unpack must not start before
+ * the matching pack has completed (same stream, an event, or a
+ * synchronisation in between). */
+typedef enum {
+  LBM_HALO_DENS = 0,     /* pack: the (rho, phi) plane next to the face; unpack: into the halo plane */
+  LBM_HALO_POP_IN = 1,   /* pack: boundary plane, populations leaving through the face; unpack: into the ghost plane */
+  LBM_HALO_POP_OUT = 2   /* pack: ghost plane, populations leaving through the face; unpack: into the boundary plane */
+} lbm_halo_phase;
+/* Bytes of one face's message of a phase (the same for both faces). */
+LBM_EXPORT lbm_status lbm_halo_bytes(const lbm* h, int phase, size_t* bytes);
+/* face: 4 = -z, 5 = +z (must be LBM_BC_HALO).  buf: device memory of
+ * lbm_halo_bytes(phase) bytes.  Asynchronous on the handle's stream. */
+LBM_EXPORT lbm_status lbm_halo_pack(lbm* h, int face, int phase, void* buf);
+LBM_EXPORT lbm_status lbm_halo_unpack(lbm* h, int face, int phase, const void* buf);
+/* One pass of one time step: pass 1 = density / phase-field pass, pass 2 =
+ * collide-stream pass (+ outflow; advances the time).  Passes alternate 1, 2,
+ * 1, 2, ... (LBM_ESTATE otherwise).  Asynchronous.  Allowed on any handle. */
+LBM_EXPORT lbm_status lbm_step_pass(lbm* h, int pass);
 
 /* Release the handle and all device memory it allocated (not a caller
  * workspace).  NULL is a no-op. */

@@ -12,6 +12,7 @@ compiles the library.
 """
 from .lbm import (Batch, Lattice, LbmError, STORAGE, SYMBOLS, library, moment_matrix, selfcheck, diag_fields_static,  # noqa: F401,E501
                   measure_fp32_peak,
-                  BC_PERIODIC, BC_NOSLIP, BC_FREESLIP, BC_INFLOW_WALL, BC_OUTFLOW)
+                  BC_PERIODIC, BC_NOSLIP, BC_FREESLIP, BC_INFLOW_WALL, BC_OUTFLOW, BC_HALO)
+from . import slabs  # noqa: F401
 from .build import build as build_library  # noqa: F401
 from .mlp import Mlp  # noqa: F401

@@ -53,6 +53,8 @@ struct lbm {
   cudaGraphExec_t graph[2];  // kGraphSteps steps starting at an even / odd step
   long long t;
   bool unstable;
+  bool halo;     // a z face is LBM_BC_HALO: the handle is one slab of a decomposed domain
+  int half;      // lbm_step_pass: 1 after pass 1 of the current step, 0 otherwise
   std::string err;
 };
 
@@ -104,7 +106,11 @@ const char* validate(int nx, int ny, int nz, const lbm_params* p) {
   }
   if (p->force_mode < 0 || p->force_mode > 3) return "unknown force_mode";
   for (int f = 0; f < 6; ++f)
-    if (p->bc[f] < 0 || p->bc[f] > 4) return "unknown boundary code";
+    if (p->bc[f] < 0 || p->bc[f] > 5) return "unknown boundary code";
+  for (int f = 0; f < 4; ++f)
+    if (p->bc[f] == LBM_BC_HALO) return "HALO faces are only allowed on -z and +z";
+  if ((p->bc[4] == LBM_BC_HALO || p->bc[5] == LBM_BC_HALO) && p->variant == 3)
+    return "slab handles (HALO faces) do not run the fused density pass (variant 3)";
   for (int a = 0; a < 3; ++a)
     if ((p->bc[2 * a] == LBM_BC_PERIODIC) != (p->bc[2 * a + 1] == LBM_BC_PERIODIC))
       return "periodic faces must come in pairs";
@@ -136,8 +142,8 @@ Layout plan(int nx, int ny, int nz, const lbm_params* p, const KernelSet* ks, in
   size_t o = 0;
   L.pop = o;
   o = align_up(o + (size_t)ks->pop_planes * 27 * Ns * ks->pop_elem_bytes, 256);
-  L.dens = o;
-  o = align_up(o + (size_t)N * ks->dens_bytes, 256);
+  L.dens = o;  // (rho, phi) with one halo plane below and above (read only across HALO faces)
+  o = align_up(o + (size_t)(N + 2 * Pn) * ks->dens_bytes, 256);
   L.fix = o;
   if (ks->has_fused) o = align_up(o + (size_t)4 * N * sizeof(int), 256);
   L.top = o;
@@ -289,7 +295,10 @@ lbm_status lbm_create(int nx, int ny, int nz, const lbm_params* p, lbm** out) {
   // scheme (the packed kernel is issue-bound, and the fused accumulation costs more
   // instructions than the density pass); the two-node kernel's register footprint
   // leaves 8 warps per SM and measured slower everywhere
-  h->variant = p->variant != 0 ? p->variant : (p->storage == LBM_STORE_F32 && nx % 32 == 0 ? 3 : 1);
+  h->halo = p->bc[4] == LBM_BC_HALO || p->bc[5] == LBM_BC_HALO;
+  h->half = 0;
+  h->variant = p->variant != 0 ? p->variant
+                               : (p->storage == LBM_STORE_F32 && nx % 32 == 0 && !h->halo ? 3 : 1);
   h->fix_ready = false;
 
   Geom& G = h->G;
@@ -341,7 +350,7 @@ lbm_status lbm_create(int nx, int ny, int nz, const lbm_params* p, lbm** out) {
     h->own_ws = true;
   }
   h->pop = h->ws + h->L.pop;
-  h->dens = h->ws + h->L.dens;
+  h->dens = h->ws + h->L.dens + (size_t)nx * ny * h->ks->dens_bytes;  // plane z = 0 (z = -1 below it)
   h->fix[0] = reinterpret_cast<unsigned long long*>(h->ws + h->L.fix);
   h->fix[1] = h->fix[0] + h->N;
   h->top = h->ws + h->L.top;
@@ -398,6 +407,7 @@ lbm_status lbm_init_fields(lbm* h, const double* rhoR, const double* rhoB, const
   }
   LBM_CUDA(h, h->ks->init(h->pop, h->G, h->P, dr, db, du, h->stream));
   h->t = 0;
+  h->half = 0;
   h->fix_ready = false;
   {
     lbm_status st = set_counter(h, 0);
@@ -429,6 +439,8 @@ lbm_status lbm_set_inflow(lbm* h, double xc, double yc, double D, double u_j0, d
 lbm_status lbm_step(lbm* h, int n) {
   if (!h || n < 0) return h ? fail(h, LBM_EINVAL, "n must be >= 0") : LBM_EINVAL;
   if (h->unstable) return fail(h, LBM_EUNSTABLE, "watchdog: non-finite or non-positive density seen");
+  if (h->halo) return fail(h, LBM_ESTATE, "slab handles (HALO faces) step with lbm_step_pass and halo exchanges");
+  if (h->half) return fail(h, LBM_ESTATE, "a step begun with lbm_step_pass(h, 1) must end with lbm_step_pass(h, 2)");
   static const bool no_graphs = getenv("LBM_NO_GRAPHS") != nullptr;
   {
     lbm_status st = ensure_fix(h, h->stream);
@@ -531,6 +543,7 @@ lbm_status lbm_set_populations(lbm* h, const double* f, long long t) {
     LBM_CUDA(h, h->ks->set_pop(h->pop, h->G, h->P, layout, i, inr, inb, h->stream));
   }
   h->t = t;
+  h->half = 0;
   h->fix_ready = false;
   {
     lbm_status st = set_counter(h, t);
@@ -547,6 +560,7 @@ lbm_status lbm_profile_step(lbm* h, int n, double* ms_out) {
   if (!h) return LBM_EINVAL;
   if (n < 1 || !ms_out) return fail(h, LBM_EINVAL, "need n >= 1 and an output array of 3 doubles");
   if (h->unstable) return fail(h, LBM_EUNSTABLE, "watchdog: non-finite or non-positive density seen");
+  if (h->halo || h->half) return fail(h, LBM_ESTATE, "not available on slab handles or between step passes");
   const bool outflow = h->p.bc[5] == LBM_BC_OUTFLOW;
   const int per = 4;
   cudaEvent_t* ev = (cudaEvent_t*)calloc((size_t)per * n, sizeof(cudaEvent_t));
@@ -689,6 +703,7 @@ lbm_status lbm_autotune(lbm* h, int steps, int* chosen) {
   if (!h) return LBM_EINVAL;
   if (steps < 1) return fail(h, LBM_EINVAL, "steps must be >= 1");
   if (h->unstable) return fail(h, LBM_EUNSTABLE, "watchdog: non-finite or non-positive density seen");
+  if (h->halo || h->half) return fail(h, LBM_ESTATE, "not available on slab handles or between step passes");
   int cand[4], nc = 0;
   cand[nc++] = 1;
   if (h->ks->has_paired && h->nx % 2 == 0) cand[nc++] = 2;
@@ -727,6 +742,112 @@ lbm_status lbm_autotune(lbm* h, int steps, int* chosen) {
   drop_graphs(h);  // captured graphs hold the kernel of the previous choice
   if (chosen) *chosen = h->variant;
   return check_flag(h);
+}
+
+lbm_status lbm_step_pass(lbm* h, int pass) {
+  if (!h) return LBM_EINVAL;
+  if (pass != 1 && pass != 2) return fail(h, LBM_EINVAL, "pass must be 1 or 2");
+  if (h->unstable) return fail(h, LBM_EUNSTABLE, "watchdog: non-finite or non-positive density seen");
+  if (pass != h->half + 1) return fail(h, LBM_ESTATE, "passes must alternate 1, 2, 1, 2, ...");
+  const long long t = h->t;
+  const int layout = (int)(t & 1);
+  cudaStream_t s = h->stream;
+  if (pass == 1) {
+    if (h->variant == 3) {
+      lbm_status st = ensure_fix(h, s);
+      if (st != LBM_OK) return st;
+      LBM_CUDA(h, cudaMemsetAsync(h->fix[layout ^ 1], 0, sizeof(unsigned long long) * (size_t)h->N, s));
+    } else {
+      h->fix_ready = false;
+      LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, nullptr, s));
+    }
+    h->half = 1;
+    return LBM_OK;
+  }
+  const bool fused = h->variant == 3;
+  LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->variant,
+                             fused ? h->fix[layout] : nullptr, fused ? h->fix[layout ^ 1] : nullptr, h->flag, s));
+  if (h->p.bc[5] == LBM_BC_OUTFLOW)
+    LBM_CUDA(h, h->ks->outflow(h->pop, h->G, h->P, layout ^ 1, h->top, fused ? h->fix[layout ^ 1] : nullptr, s));
+  h->t += 1;
+  h->half = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_halo_bytes(const lbm* h, int phase, size_t* bytes) {
+  if (!h || !bytes) return LBM_EINVAL;
+  const size_t plane = (size_t)h->nx * h->ny;
+  if (phase == LBM_HALO_DENS) {
+    *bytes = plane * h->ks->dens_bytes;
+    return LBM_OK;
+  }
+  if (phase == LBM_HALO_POP_IN || phase == LBM_HALO_POP_OUT) {
+    // 9 directions per stored colour plane set, whole 32-node storage blocks of one z plane
+    *bytes = (size_t)h->ks->pop_planes * 9 * (size_t)h->G.nxs * h->ny * h->ks->pop_elem_bytes;
+    return LBM_OK;
+  }
+  return LBM_EINVAL;
+}
+
+namespace {
+
+// One face's message: the slots of one z plane that hold the populations moving across the
+// face from the packing slab to the unpacking one (down through the packer's -z face, up
+// through its +z face), 9 directions per stored colour.
+//   POP_IN  (after an even step, layout 1: a slot's stored direction is opposite to the motion
+//           of the population it holds) pack: the boundary plane; unpack: the ghost plane.
+//   POP_OUT (after an odd step, layout 0: stored direction = motion) pack: the ghost plane the
+//           odd step wrote into; unpack: the boundary plane.
+// Stored directions are in tensor order t = (cx+1) + 3(cy+1) + 9(cz+1): c_z = -1 is t = 0..8,
+// c_z = +1 is t = 18..26.
+lbm_status halo_copy(lbm* h, int face, int phase, bool pack, char* buf) {
+  if (face != 4 && face != 5) return fail(h, LBM_EINVAL, "face must be 4 (-z) or 5 (+z)");
+  if (h->p.bc[face] != LBM_BC_HALO) return fail(h, LBM_ESTATE, "face %d is not LBM_BC_HALO", face);
+  if (!buf) return fail(h, LBM_EINVAL, "buffer is NULL");
+  cudaStream_t s = h->stream;
+  const bool lo = face == 4;
+  if (phase == LBM_HALO_DENS) {
+    const size_t plane = (size_t)h->nx * h->ny * h->ks->dens_bytes;
+    // pack: the plane next to the face; unpack: the halo plane beyond it
+    const long long z = pack ? (lo ? 0 : h->nz - 1) : (lo ? -1 : h->nz);
+    char* d = static_cast<char*>(h->dens) + z * (long long)plane;
+    if (pack) LBM_CUDA(h, cudaMemcpyAsync(buf, d, plane, cudaMemcpyDeviceToDevice, s));
+    else LBM_CUDA(h, cudaMemcpyAsync(d, buf, plane, cudaMemcpyDeviceToDevice, s));
+    return LBM_OK;
+  }
+  if (phase != LBM_HALO_POP_IN && phase != LBM_HALO_POP_OUT) return fail(h, LBM_EINVAL, "unknown halo phase");
+  const bool in = phase == LBM_HALO_POP_IN;
+  const bool boundary = in == pack;  // the boundary plane (else the ghost plane beyond the face)
+  const int z = boundary ? (lo ? 0 : h->nz - 1) : (lo ? -1 : h->nz);
+  const bool down = pack ? lo : !lo;  // the message's populations move towards -z
+  const bool stored_down = in ? !down : down;
+  const int t0 = stored_down ? 0 : 18;
+  const size_t e = h->ks->pop_elem_bytes;
+  const int planes = 27 * h->ks->pop_planes;
+  const size_t nblocks = (size_t)h->G.nxs * h->ny / 32;
+  const size_t block0 = (size_t)h->G.nxs * h->ny * (size_t)(z + 1) / 32;  // storage plane z + 1
+  const size_t width = 9 * 32 * e, spitch = (size_t)planes * 32 * e;
+  for (int c = 0; c < h->ks->pop_planes; ++c) {
+    char* slab = static_cast<char*>(h->pop) + (block0 * planes + (size_t)(c * 27 + t0)) * 32 * e;
+    char* msg = buf + (size_t)c * nblocks * width;
+    if (pack)
+      LBM_CUDA(h, cudaMemcpy2DAsync(msg, width, slab, spitch, width, nblocks, cudaMemcpyDeviceToDevice, s));
+    else
+      LBM_CUDA(h, cudaMemcpy2DAsync(slab, spitch, msg, width, width, nblocks, cudaMemcpyDeviceToDevice, s));
+  }
+  return LBM_OK;
+}
+
+}  // namespace
+
+lbm_status lbm_halo_pack(lbm* h, int face, int phase, void* buf) {
+  if (!h) return LBM_EINVAL;
+  return halo_copy(h, face, phase, true, static_cast<char*>(buf));
+}
+
+lbm_status lbm_halo_unpack(lbm* h, int face, int phase, const void* buf) {
+  if (!h) return LBM_EINVAL;
+  return halo_copy(h, face, phase, false, const_cast<char*>(static_cast<const char*>(buf)));
 }
 
 void lbm_free(lbm* h) {
@@ -807,7 +928,7 @@ lbm_status lbm_batch_create(lbm* const* handles, int n, void* cuda_stream, lbm_b
   *out = nullptr;
   if (!handles || n < 1) return LBM_EINVAL;
   for (int i = 0; i < n; ++i)
-    if (!handles[i]) return LBM_EINVAL;
+    if (!handles[i] || handles[i]->halo) return LBM_EINVAL;
   lbm_batch* b = new (std::nothrow) lbm_batch();
   if (!b) return LBM_ENOMEM;
   b->h.assign(handles, handles + n);
@@ -834,7 +955,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int n) {
   if (!b || n < 0) return LBM_EINVAL;
   const long long t0 = b->h[0]->t;
   for (lbm* h : b->h) {
-    if (((h->t - t0) & 1) != 0) return LBM_ESTATE;
+    if (((h->t - t0) & 1) != 0 || h->half) return LBM_ESTATE;
     if (h->unstable) return LBM_EUNSTABLE;
   }
   // the batch stream first waits for whatever each handle's own stream has queued ...

@@ -34,7 +34,7 @@
 
 namespace lbmk {
 
-enum { BC_PERIODIC = 0, BC_NOSLIP = 1, BC_FREESLIP = 2, BC_INFLOW_WALL = 3, BC_OUTFLOW = 4 };
+enum { BC_PERIODIC = 0, BC_NOSLIP = 1, BC_FREESLIP = 2, BC_INFLOW_WALL = 3, BC_OUTFLOW = 4, BC_HALO = 5 };
 enum { FORCE_NONE = 0, FORCE_BUOYANCY = 1, FORCE_DISPERSED = 2, FORCE_UNIFORM = 3 };
 
 constexpr int BX = 32, BY = 4, BZ = 2;  // pass-2 block: one thread per node
@@ -177,8 +177,9 @@ struct NodeMap {
         if (bc == BC_PERIODIC) off_p[a] = -(n[a] - 1) * stride[a];
         else if (bc == BC_NOSLIP) bounce_p |= 1u << a;
         else if (bc == BC_FREESLIP || bc == BC_INFLOW_WALL) { off_p[a] = 0; flip_p |= 1u << a; }
-        // BC_OUTFLOW: off_p stays +stride and lands in the ghost plane z = nz
+        // BC_OUTFLOW and BC_HALO: off_p stays +stride and lands in the ghost plane z = nz
       }
+      // BC_HALO at the low face: off_m stays -stride and lands in the ghost plane z = -1
     }
   }
 
@@ -605,11 +606,17 @@ __device__ __forceinline__ void inlet_state(const KConst<R>& K, int64_t node_lin
   }
 }
 
+// coordinate of the (rho, phi) value a tile cell reads along one axis: wrapped on periodic
+// faces, the halo plane (-1 or n, filled by the neighbouring slab) on halo faces, else the
+// mirror ghost of a wall (the index clamped into the box)
 __device__ __forceinline__ int wrap_or_clamp(int q, int n, int bc_lo, int bc_hi) {
-  if (q < 0) return bc_lo == BC_PERIODIC ? q + n : 0;
-  if (q >= n) return bc_hi == BC_PERIODIC ? q - n : n - 1;
+  if (q < 0) return bc_lo == BC_PERIODIC ? q + n : (bc_lo == BC_HALO ? -1 : 0);
+  if (q >= n) return bc_hi == BC_PERIODIC ? q - n : (bc_hi == BC_HALO ? n : n - 1);
   return q;
 }
+// the last z plane a tile row may read: nz - 1, or the halo plane nz above a halo face
+// (rows past it belong to the ragged tail of the last block and read a clamped row)
+__device__ __forceinline__ int tile_zmax(const Geom& G) { return G.bc[5] == BC_HALO ? G.nz : G.nz - 1; }
 
 // ---------------------------------------------------------------------------
 // Fused density pass.  The density of node y at t+1 is the sum of the
@@ -954,7 +961,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
         const int gy = wrap_or_clamp(y0 + ty - 1, G.ny, G.bc[2], G.bc[3]);
         const int gz = wrap_or_clamp(z0 + tz - 1, G.nz, G.bc[4], G.bc[5]);
         // out-of-box tail rows of a ragged block read a clamped in-box row
-        const int cy = gy < G.ny ? gy : G.ny - 1, cz = gz < G.nz ? gz : G.nz - 1;
+        const int cy = gy < G.ny ? gy : G.ny - 1, cz = gz <= tile_zmax(G) ? gz : tile_zmax(G);
         const int64_t rbase = (int64_t)G.nx * ((int64_t)cy + (int64_t)G.ny * cz);
         if constexpr (FUSED) {
           tile[row * TX + lane] = fused_cell(io, rbase + cxa);
@@ -1142,7 +1149,7 @@ __device__ __forceinline__ void pf_issue(const uint32_t* A, const Geom& G, const
       const int gy = wrap_or_clamp(y0 + row % TY - 1, G.ny, G.bc[2], G.bc[3]);
       const int gz = wrap_or_clamp(z0 + row / TY - 1, G.nz, G.bc[4], G.bc[5]);
       const int64_t rbase = (int64_t)G.nx * ((int64_t)(gy < G.ny ? gy : G.ny - 1) +
-                                              (int64_t)G.ny * (gz < G.nz ? gz : G.nz - 1));
+                                              (int64_t)G.ny * (gz <= tile_zmax(G) ? gz : tile_zmax(G)));
       cp_async8(tile_s + row * TX + lane, dens + rbase + cxa);
       if (lane < TX - 32) cp_async8(tile_s + row * TX + 32 + lane, dens + rbase + cxb);
     }
@@ -1331,7 +1338,7 @@ __global__ void __launch_bounds__(PTHREADS, MINB)
         const int gy = wrap_or_clamp(y0 + ty - 1, G.ny, G.bc[2], G.bc[3]);
         const int gz = wrap_or_clamp(z0 + tz - 1, G.nz, G.bc[4], G.bc[5]);
         const int64_t rbase = (int64_t)G.nx * ((int64_t)(gy < G.ny ? gy : G.ny - 1) +
-                                                (int64_t)G.ny * (gz < G.nz ? gz : G.nz - 1));
+                                                (int64_t)G.ny * (gz <= tile_zmax(G) ? gz : tile_zmax(G)));
         tile[row * TX + lane] = dens[rbase + cxl];
         if (lane < TX - 32) tile[row * TX + 32 + lane] = dens[rbase + cxr];
       }

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
 
 STORE_F64, STORE_F32, STORE_F16, STORE_BF16 = range(4)
 STORAGE = {"f64": STORE_F64, "f32": STORE_F32, "f16": STORE_F16, "bf16": STORE_BF16}
-BC_PERIODIC, BC_NOSLIP, BC_FREESLIP, BC_INFLOW_WALL, BC_OUTFLOW = range(5)
+BC_PERIODIC, BC_NOSLIP, BC_FREESLIP, BC_INFLOW_WALL, BC_OUTFLOW, BC_HALO = range(6)
 STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA", -4: "LBM_EUNSTABLE",
           -5: "LBM_ETIMEOUT", -6: "LBM_ESTATE"}
 Q = 27
@@ -27,7 +27,8 @@ SYMBOLS = ["lbm_workspace_size", "lbm_create", "lbm_init_fields", "lbm_set_inflo
            "lbm_diag", "lbm_get_populations", "lbm_set_populations", "lbm_profile_step", "lbm_set_stream", "lbm_synchronize", "lbm_time",
            "lbm_kernels_per_step", "lbm_last_error", "lbm_status_string", "lbm_moment_matrix", "lbm_selfcheck",
            "lbm_diag_fields_static", "lbm_autotune", "lbm_batch_create", "lbm_batch_step", "lbm_batch_synchronize",
-           "lbm_batch_free", "lbm_measure_fp32_peak", "lbm_kernel_variant", "lbm_free"]
+           "lbm_batch_free", "lbm_measure_fp32_peak", "lbm_kernel_variant", "lbm_halo_bytes", "lbm_halo_pack",
+           "lbm_halo_unpack", "lbm_step_pass", "lbm_free"]
 
 
 class LbmError(RuntimeError):
@@ -96,6 +97,10 @@ def library():
         lib.lbm_batch_free.argtypes = [h]
         lib.lbm_batch_free.restype = None
         lib.lbm_measure_fp32_peak.argtypes = [vp, i, P(d)]
+        lib.lbm_halo_bytes.argtypes = [h, i, P(ctypes.c_size_t)]
+        lib.lbm_halo_pack.argtypes = [h, i, i, vp]
+        lib.lbm_halo_unpack.argtypes = [h, i, i, vp]
+        lib.lbm_step_pass.argtypes = [h, i]
         lib.lbm_free.argtypes = [h]
         lib.lbm_free.restype = None
         for name in SYMBOLS:
@@ -290,6 +295,25 @@ class Lattice:
     def step(self, n=1):
         _check(library().lbm_step(self._h, int(n)), self._h)
 
+    def step_pass(self, p):
+        """One pass of a time step: 1 = density pass, 2 = collide-stream (+ outflow; the time advances)."""
+        _check(library().lbm_step_pass(self._h, int(p)), self._h)
+
+    # -- z-slab halo exchange (see paper_1705_03141_gb300.slabs) ----------
+    def halo_bytes(self, phase):
+        n = ctypes.c_size_t()
+        _check(library().lbm_halo_bytes(self._h, int(phase), ctypes.byref(n)), self._h)
+        return int(n.value)
+
+    def halo_pack(self, face, phase, buf):
+        """Copy one face's message into `buf` (a uint8 device tensor of halo_bytes(phase) bytes)."""
+        _check(library().lbm_halo_pack(self._h, int(face), int(phase), _dev_ptr(buf, self.halo_bytes(phase))),
+               self._h)
+
+    def halo_unpack(self, face, phase, buf):
+        _check(library().lbm_halo_unpack(self._h, int(face), int(phase), _dev_ptr(buf, self.halo_bytes(phase))),
+               self._h)
+
     def profile_step(self, n):
         """Take n steps with per-launch CUDA-event timing; mean ms per launch of
         (density pass, collide-stream pass, outflow pass)."""
@@ -370,6 +394,15 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _dev_ptr(buf, nbytes):
+    """Device pointer of a contiguous CUDA tensor holding at least nbytes bytes."""
+    import torch
+
+    assert isinstance(buf, torch.Tensor) and buf.is_cuda and buf.is_contiguous()
+    assert buf.numel() * buf.element_size() >= nbytes, "halo buffer too small"
+    return buf.data_ptr()
 
 
 def _as_f64(a):

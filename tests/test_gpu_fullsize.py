@@ -72,7 +72,7 @@ def test_fullsize_packed(cuda, reference, storage):
     scale = max(np.max(np.abs(orr)), np.max(np.abs(orb)))
     assert np.max(np.abs(gr - orr)) < tol * scale
     assert np.max(np.abs(gb - orb)) < tol * scale
-    _check_packed_velocity(gu, ou, storage, f"full-size jet {storage}")
+    _check_packed_velocity(gu, ou, storage, f"full-size jet {storage}", scale)
 
 
 @pytest.mark.parametrize("storage,tol_sym,tol_mass", [("f32", 1e-5, 1e-6), ("f16", 2e-3, 1e-4)])

@@ -6,10 +6,13 @@ oracle to 1e-12), on the paper's own set-ups, through the C ABI:
     bfloat16 within 3e-2 (relative); every storage keeps sigma from Laplace's law within 10 %
     of Eq. (sigma), the finite-radius error of the FP64 run itself (6-7 % at R = 8);
   * leading edge of a half-scale jet (Sec. IV.A: 64 x 64 x 256, nozzle D = 8, u_j0 = 0.115,
-    gamma = 1.2, eta = 3, 4000 steps, sampled every 500): FP32 within 0.01 D of FP64 at
-    every sample, half within 0.05 D, bfloat16 within 0.3 D.
+    gamma = 1.2, eta = 3, 2000 steps = 29 D/u_j0, sampled every 500, the tip at 15 D): FP32
+    within 0.01 D of FP64 at every sample, half within 0.05 D, bfloat16 within 0.3 D.
 
-These are the budgets the benchmark's headline storage is held to.
+These are the budgets the benchmark's headline storage is held to.  The jet's own instability
+amplifies any perturbation, rounding included (FP32 and FP64 storage part by 0.1 D near
+t u_j0/D = 47 on the full jet), so a leading-edge budget holds up to a stated time: here 29 D/u_j0
+(half storage departs by 0.34 D by 57 D/u_j0).
 """
 import numpy as np
 import pytest
@@ -61,7 +64,7 @@ def test_laplace_pressure_within_budget(cuda, laplace64, storage):
     assert e64 < 0.10 and e < 0.10
 
 
-def _jet_edges(storage, steps=4000, every=500):
+def _jet_edges(storage, steps=2000, every=500):
     w = L.jet(nx=64, ny=64, nz=256, D=8.0, Re=1700.0)
     rr, rb, u = L.initial_fields(w)
     lat = pkg.Lattice(w["shape"], w["params"], storage=storage)
