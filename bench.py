@@ -47,8 +47,11 @@ UNIT = "MLUPS"
 # algorithmic bytes per node and step of each kernel:
 #   density pass: read 54 populations, write (rho, phi)
 #   collide-stream pass: read (rho, phi) once, read and write 54 populations
-POP_BYTES = {"f64": 8 * 54, "f32": 4 * 54, "f16": 4 * 27, "bf16": 4 * 27}
-DENS_BYTES = {"f64": 16, "f32": 8, "f16": 8, "bf16": 8}
+#   compact storages (c16, cbf16): 26 x 2 + 4 bytes of totals, and the node's colour record
+#   (16 bytes) written by the collide-stream pass and read (once per node) by the density pass
+POP_BYTES = {"f64": 8 * 54, "f32": 4 * 54, "f16": 4 * 27, "bf16": 4 * 27, "c16": 56, "cbf16": 56}
+DENS_BYTES = {"f64": 16, "f32": 8, "f16": 8, "bf16": 8, "c16": 8, "cbf16": 8}
+RECORD_BYTES = {"c16": 16, "cbf16": 16}
 
 
 def workload(seed=1234):
@@ -84,7 +87,7 @@ def collide_bytes(storage, variant):
     """Algorithmic bytes per node of one collide-stream launch: every population read and written
     once, plus (rho, phi) of pass 1 (two-pass) or the fixed-point (rho, rho_r) read and the next
     step's written once (fused density pass, 2 x 8 bytes)."""
-    return POP_BYTES[storage] * 2 + (16 if variant == 3 else DENS_BYTES[storage])
+    return POP_BYTES[storage] * 2 + (16 if variant == 3 else DENS_BYTES[storage]) + RECORD_BYTES.get(storage, 0)
 
 
 def profiled(storage, key, variant=1):
@@ -369,7 +372,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--storage", default="f16", choices=["f16", "bf16", "f32"])
+    ap.add_argument("--storage", default="f16", choices=["f16", "bf16", "f32", "c16", "cbf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -61,12 +61,23 @@ typedef enum {
  * matches the FP64 CPU oracle.  LBM_STORE_F16 / LBM_STORE_BF16 keep, per
  * direction and node, the total population as a deviation from its
  * rest-state value in half / bfloat16 plus the red fraction f^r/f as an
- * unsigned 16-bit fixed-point number (4 bytes per direction and node). */
+ * unsigned 16-bit fixed-point number (4 bytes per direction and node).
+ * LBM_STORE_F16C / LBM_STORE_BF16C (compact) keep the total population of
+ * each moving direction as a half / bfloat16 deviation from its rest value
+ * (2 bytes), the rest direction's total in FP32, and one FP32 record per node
+ * (frac, m) from which the recolouring of Sec. II fixes the colour split of
+ * everything the node emitted: f^r_i = frac f_i + (w_i/|c_i|) c_i.m (72 bytes
+ * per node in all).  Compact storage runs collide-stream variant 1 only and
+ * has no z-slab exchange; after lbm_init_fields or lbm_set_populations its
+ * per-colour populations are available again (lbm_get_populations) after the
+ * first step. */
 typedef enum {
   LBM_STORE_F64 = 0,
   LBM_STORE_F32 = 1,
   LBM_STORE_F16 = 2,
-  LBM_STORE_BF16 = 3
+  LBM_STORE_BF16 = 3,
+  LBM_STORE_F16C = 4,
+  LBM_STORE_BF16C = 5
 } lbm_storage;
 
 /* Face conditions, faces ordered (-x, +x, -y, +y, -z, +z).

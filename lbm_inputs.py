@@ -201,13 +201,37 @@ def regime_label(Re, Oh, We):
     return 3
 
 
-def regime_sweep(n=64, seed=2024, steps=20000, eta=3.0, Fr=8.5, A_max=0.02, nu_max=0.015, u_max=0.1):
-    """`n` jets (configs of the batched sweep): grids nx = ny in {64, 80, 96} with nz = 4 nx, nozzle
-    D in 8..12, (Re, Oh) log-uniform over [10, 3e3] x [1e-3, 1], gamma uniform in [1.1, 1.5],
-    eta = 3, Fr = 8.5.  Lattice mapping: nu_j = min(u_max D/Re, nu_max) (nu_max keeps the MRT with
+def jet_from_groups(Re, Oh, gamma, eta, D=10.0, nxy=80, nz=None, Fr=8.5, A_max=0.02, nu_max=0.015, u_max=0.1,
+                    noise=0.01, seed=0, steps=20000, name=None):
+    """A jet with the given dimensionless groups (Sec. IV.B) on a lattice: nozzle D, box nxy x nxy x nz
+    (nz = 4 nxy by default).  Lattice mapping: nu_j = min(u_max D/Re, nu_max) (nu_max keeps the MRT with
     Suga's rates in its stable range), u_j0 = Re nu_j / D, nu_c = nu_j/eta, We = (Re Oh)^2,
-    sigma = rho_j u_j0^2 D / We, A = 9 sigma / (4 tau) with tau at the interface, capped at A_max
-    (the achieved Oh is recorded), g = u_j0^2/(Fr D)."""
+    sigma = rho_j u_j0^2 D / We, A = 9 sigma / (4 tau) with tau at the interface, capped at A_max (the
+    achieved Oh and We are recorded), g = u_j0^2/(Fr D)."""
+    nz = 4 * nxy if nz is None else nz
+    nu_j = min(u_max * D / Re, nu_max)
+    u = Re * nu_j / D
+    nu_c = nu_j / eta
+    We = (Re * Oh) ** 2
+    sigma = u * u * D / We
+    tau = 3.0 * 0.5 * (nu_j + nu_c) + 0.5
+    A = min(9.0 * sigma / (4.0 * tau), A_max)
+    sigma_eff = 4.0 / 9.0 * A * tau
+    We_eff = u * u * D / sigma_eff
+    Oh_eff = math.sqrt(We_eff) / Re
+    w = jet(nx=nxy, ny=nxy, nz=nz, D=D, Re=Re, nu_c=nu_c, gamma=gamma, eta=eta, A=A, Fr=Fr, noise=noise, seed=seed)
+    w["name"] = name or f"jet_Re{Re:.3g}_Oh{Oh:.3g}_{nxy}x{nxy}x{nz}_D{D:g}"
+    w["steps"] = steps
+    w["groups"] = dict(Re=Re, Oh=Oh_eff, We=We_eff, gamma=gamma, eta=eta, Oh_target=Oh,
+                       regime=regime_label(Re, Oh_eff, We_eff), u_j0=u, D=D)
+    return w
+
+
+def regime_sweep(n=64, seed=2024, steps=20000, eta=None, Fr=8.5, A_max=0.02, nu_max=0.015, u_max=0.1):
+    """`n` jets (configs of the batched sweep): grids nx = ny in {64, 80, 96} with nz = 4 nx, nozzle
+    D in 8..12, (Re, Oh) log-uniform over [10, 3e3] x [1e-3, 1], gamma uniform in [1.1, 1.5], the
+    viscosity ratio eta uniform in [1, 5] (or fixed when given), Fr = 8.5; lattice mapping as in
+    jet_from_groups."""
     rng = np.random.default_rng(seed)
     out = []
     for k in range(n):
@@ -216,21 +240,8 @@ def regime_sweep(n=64, seed=2024, steps=20000, eta=3.0, Fr=8.5, A_max=0.02, nu_m
         Re = float(10 ** rng.uniform(1.0, math.log10(3e3)))
         Oh = float(10 ** rng.uniform(-3.0, 0.0))
         gamma = float(rng.uniform(1.1, 1.5))
-        nu_j = min(u_max * D / Re, nu_max)
-        u = Re * nu_j / D
-        nu_c = nu_j / eta
-        We = (Re * Oh) ** 2
-        sigma = u * u * D / We
-        tau = 3.0 * 0.5 * (nu_j + nu_c) + 0.5
-        A = min(9.0 * sigma / (4.0 * tau), A_max)
-        sigma_eff = 4.0 / 9.0 * A * tau
-        We_eff = u * u * D / sigma_eff
-        Oh_eff = math.sqrt(We_eff) / Re
-        w = jet(nx=nxy, ny=nxy, nz=4 * nxy, D=D, Re=Re, nu_c=nu_c, gamma=gamma, eta=eta, A=A, Fr=Fr,
-                noise=0.01, seed=seed * 1000 + k)
-        w["name"] = f"sweep_{k:02d}_{nxy}x{nxy}x{4 * nxy}_D{D:g}"
-        w["steps"] = steps
-        w["groups"] = dict(Re=Re, Oh=Oh_eff, We=We_eff, gamma=gamma, eta=eta, Oh_target=Oh,
-                           regime=regime_label(Re, Oh_eff, We_eff), u_j0=u, D=D)
-        out.append(w)
+        eta_k = float(rng.uniform(1.0, 5.0)) if eta is None else float(eta)
+        out.append(jet_from_groups(Re, Oh, gamma, eta_k, D=D, nxy=nxy, Fr=Fr, A_max=A_max, nu_max=nu_max,
+                                   u_max=u_max, seed=seed * 1000 + k, steps=steps,
+                                   name=f"sweep_{k:02d}_{nxy}x{nxy}x{4 * nxy}_D{D:g}"))
     return out

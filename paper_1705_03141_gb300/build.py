@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbm.so")
-SOURCES = ["lbm_capi.cu", "lbm_kernels_f64.cu", "lbm_kernels_f32.cu", "lbm_kernels_f16.cu", "lbm_static_diag.cu", "lbm_peak.cu", "lbm_mlp.cu"]
+SOURCES = ["lbm_capi.cu", "lbm_kernels_f64.cu", "lbm_kernels_f32.cu", "lbm_kernels_f16.cu", "lbm_kernels_c16.cu", "lbm_static_diag.cu", "lbm_peak.cu", "lbm_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

@@ -54,6 +54,8 @@ struct lbm {
   long long t;
   bool unstable;
   bool halo;     // a z face is LBM_BC_HALO: the handle is one slab of a decomposed domain
+  bool recs_valid;  // compact storage: the colour records describe the current state
+  bool dens_ready;  // compact storage: dens holds (rho, phi) of the current state
   int half;      // lbm_step_pass: 1 after pass 1 of the current step, 0 otherwise
   std::string err;
 };
@@ -84,6 +86,8 @@ const KernelSet* kernels_for(int storage) {
     case LBM_STORE_F32: return lbmk::kernels_f32();
     case LBM_STORE_F16: return lbmk::kernels_f16();
     case LBM_STORE_BF16: return lbmk::kernels_bf16();
+    case LBM_STORE_F16C: return lbmk::kernels_c16();
+    case LBM_STORE_BF16C: return lbmk::kernels_cbf16();
     default: return nullptr;
   }
 }
@@ -118,7 +122,11 @@ const char* validate(int nx, int ny, int nz, const lbm_params* p) {
     if (p->bc[f] == LBM_BC_INFLOW_WALL && f != 4) return "INFLOW_WALL is only allowed on the -z face";
     if (p->bc[f] == LBM_BC_OUTFLOW && f != 5) return "OUTFLOW is only allowed on the +z face";
   }
-  if (p->storage < 0 || p->storage > 3) return "unknown storage";
+  if (p->storage < 0 || p->storage > 5) return "unknown storage";
+  if (p->storage == LBM_STORE_F16C || p->storage == LBM_STORE_BF16C) {
+    if (p->variant > 1) return "compact storage runs the one-node collide-stream kernel (variant 0 or 1)";
+    if (p->bc[4] == LBM_BC_HALO || p->bc[5] == LBM_BC_HALO) return "compact storage has no z-slab halo exchange";
+  }
   if (p->variant < 0 || p->variant > 4) return "unknown kernel variant";
   if (p->variant == 4 && p->storage != LBM_STORE_F16 && p->storage != LBM_STORE_BF16)
     return "the software-pipelined kernel needs packed (F16/BF16) storage";
@@ -141,7 +149,7 @@ Layout plan(int nx, int ny, int nz, const lbm_params* p, const KernelSet* ks, in
   Layout L;
   size_t o = 0;
   L.pop = o;
-  o = align_up(o + (size_t)ks->pop_planes * 27 * Ns * ks->pop_elem_bytes, 256);
+  o = align_up(o + (size_t)Ns * ks->pop_node_bytes, 256);
   L.dens = o;  // (rho, phi) with one halo plane below and above (read only across HALO faces)
   o = align_up(o + (size_t)(N + 2 * Pn) * ks->dens_bytes, 256);
   L.fix = o;
@@ -187,8 +195,9 @@ void drop_graphs(lbm* h) {
     }
 }
 
-// enqueue one time step (the step with index t) on stream s
-lbm_status enqueue_step(lbm* h, long long t, cudaStream_t s) {
+// enqueue one time step (the step with index t) on stream s; skip_density: the (rho, phi)
+// field already holds the state's densities (first step of compact storage after an upload)
+lbm_status enqueue_step(lbm* h, long long t, cudaStream_t s, bool skip_density = false) {
   const int layout = (int)(t & 1);
   const bool outflow = h->p.bc[5] == LBM_BC_OUTFLOW;
   if (h->variant == 3) {
@@ -200,7 +209,7 @@ lbm_status enqueue_step(lbm* h, long long t, cudaStream_t s) {
     return LBM_OK;
   }
   h->fix_ready = false;  // steps without the fused pass leave its accumulators behind
-  LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, nullptr, s));
+  if (!skip_density) LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, nullptr, s));
   LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->variant, nullptr, nullptr,
                              h->flag, s));
   if (outflow) LBM_CUDA(h, h->ks->outflow(h->pop, h->G, h->P, layout ^ 1, h->top, nullptr, s));
@@ -238,6 +247,26 @@ lbm_status build_graph(lbm* h, int parity) {
     h->graph[parity] = nullptr;
     return fail(h, LBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
   }
+  return LBM_OK;
+}
+
+// compact storage: the state uploaded by lbm_init_fields / lbm_set_populations has no colour
+// records; its first step takes (rho, phi) as written by the upload instead of running pass 1
+lbm_status compact_first_step(lbm* h, cudaStream_t s) {
+  LBM_CUDA(h, cudaGetLastError());
+  lbm_status st = enqueue_step(h, h->t, s, true);
+  if (st != LBM_OK) return st;
+  h->t += 1;
+  h->recs_valid = true;
+  h->dens_ready = false;
+  return LBM_OK;
+}
+
+// compact storage: (rho, phi) of the current state in dens (pass 1, if not already there)
+lbm_status compact_dens(lbm* h) {
+  if (!h->ks->compact || h->dens_ready) return LBM_OK;
+  LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, (int)(h->t & 1), h->dens, h->flag, nullptr, h->stream));
+  h->dens_ready = true;
   return LBM_OK;
 }
 
@@ -297,6 +326,8 @@ lbm_status lbm_create(int nx, int ny, int nz, const lbm_params* p, lbm** out) {
   // leaves 8 warps per SM and measured slower everywhere
   h->halo = p->bc[4] == LBM_BC_HALO || p->bc[5] == LBM_BC_HALO;
   h->half = 0;
+  h->recs_valid = false;
+  h->dens_ready = false;
   h->variant = p->variant != 0 ? p->variant
                                : (p->storage == LBM_STORE_F32 && nx % 32 == 0 && !h->halo ? 3 : 1);
   h->fix_ready = false;
@@ -310,6 +341,7 @@ lbm_status lbm_create(int nx, int ny, int nz, const lbm_params* p, lbm** out) {
   for (int f = 0; f < 6; ++f) G.bc[f] = p->bc[f];
   G.inflow = 0;
   G.xc = G.yc = G.r2 = 0.0;
+  G.ctop = nullptr;
 
   Phys& P = h->P;
   memset(&P, 0, sizeof P);
@@ -354,6 +386,7 @@ lbm_status lbm_create(int nx, int ny, int nz, const lbm_params* p, lbm** out) {
   h->fix[0] = reinterpret_cast<unsigned long long*>(h->ws + h->L.fix);
   h->fix[1] = h->fix[0] + h->N;
   h->top = h->ws + h->L.top;
+  if (h->ks->compact && p->bc[5] == LBM_BC_OUTFLOW) h->G.ctop = static_cast<float*>(h->top);
   h->counter = reinterpret_cast<long long*>(h->ws + h->L.counter);
   h->flag = reinterpret_cast<int*>(h->ws + h->L.flag);
   h->partial = h->ws + h->L.partial;
@@ -363,6 +396,13 @@ lbm_status lbm_create(int nx, int ny, int nz, const lbm_params* p, lbm** out) {
     cudaGetLastError();
     if (h->own_ws) cudaFree(h->ws);
     delete h;
+    return LBM_ECUDA;
+  }
+  if (h->ks->compact &&  // colour records: defined contents before the first step writes them
+      cudaMemsetAsync(static_cast<char*>(h->pop) + (size_t)56 * h->G.Ns, 0, (size_t)16 * h->G.Ns, h->stream) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    lbm_free(h);
     return LBM_ECUDA;
   }
   // initial state: pure blue fluid at rest
@@ -405,7 +445,14 @@ lbm_status lbm_init_fields(lbm* h, const double* rhoR, const double* rhoB, const
     LBM_CUDA(h, cudaMemcpyAsync(su, u, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, h->stream));
     du = su;
   }
-  LBM_CUDA(h, h->ks->init(h->pop, h->G, h->P, dr, db, du, h->stream));
+  if (h->ks->compact) {
+    // totals, (rho, phi) and the top plane's colours; the first step takes (rho, phi) as given
+    LBM_CUDA(h, h->ks->init_c(h->pop, h->G, h->P, dr, db, du, h->dens, h->stream));
+    h->dens_ready = true;
+    h->recs_valid = false;
+  } else {
+    LBM_CUDA(h, h->ks->init(h->pop, h->G, h->P, dr, db, du, h->stream));
+  }
   h->t = 0;
   h->half = 0;
   h->fix_ready = false;
@@ -414,7 +461,8 @@ lbm_status lbm_init_fields(lbm* h, const double* rhoR, const double* rhoB, const
     if (st != LBM_OK) return st;
   }
   LBM_CUDA(h, cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
-  if (h->p.bc[5] == LBM_BC_OUTFLOW) LBM_CUDA(h, h->ks->top_from_state(h->pop, h->G, h->P, 0, h->top, h->stream));
+  if (h->p.bc[5] == LBM_BC_OUTFLOW && !h->ks->compact)
+    LBM_CUDA(h, h->ks->top_from_state(h->pop, h->G, h->P, 0, h->top, h->stream));
   LBM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->unstable = false;
   return LBM_OK;
@@ -447,6 +495,14 @@ lbm_status lbm_step(lbm* h, int n) {
     if (st != LBM_OK) return st;
   }
   int k = 0;
+  if (h->ks->compact && n > 0) {
+    if (!h->recs_valid) {
+      lbm_status st = compact_first_step(h, h->stream);
+      if (st != LBM_OK) return st;
+      k = 1;
+    }
+    h->dens_ready = false;
+  }
   if (!no_graphs && n >= kGraphSteps) {
     const int parity = (int)(h->t & 1);
     if (!h->graph[parity]) {
@@ -473,7 +529,13 @@ lbm_status lbm_macro(lbm* h, double* rhoR, double* rhoB, double* u) {
   double* dr = rhoR ? (is_device_ptr(rhoR) ? rhoR : h->scratch) : nullptr;
   double* db = rhoB ? (is_device_ptr(rhoB) ? rhoB : h->scratch + N) : nullptr;
   double* du = u ? (is_device_ptr(u) ? u : h->scratch + 2 * N) : nullptr;
-  LBM_CUDA(h, h->ks->macro(h->pop, h->G, h->P, layout, dr, db, du, h->stream));
+  if (h->ks->compact) {
+    lbm_status st = compact_dens(h);
+    if (st != LBM_OK) return st;
+    LBM_CUDA(h, h->ks->macro_c(h->pop, h->G, h->P, layout, h->dens, dr, db, du, h->stream));
+  } else {
+    LBM_CUDA(h, h->ks->macro(h->pop, h->G, h->P, layout, dr, db, du, h->stream));
+  }
   if (rhoR && dr != rhoR) LBM_CUDA(h, cudaMemcpyAsync(rhoR, dr, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
   if (rhoB && db != rhoB) LBM_CUDA(h, cudaMemcpyAsync(rhoB, db, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
   if (u && du != u) LBM_CUDA(h, cudaMemcpyAsync(u, du, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, h->stream));
@@ -486,7 +548,13 @@ lbm_status lbm_diag(lbm* h, double* mass_rb, double* z_leading_edge, double* dp_
   const int layout = (int)(h->t & 1);
   double* rr = h->scratch;
   double* rb = h->scratch + N;
-  LBM_CUDA(h, h->ks->macro(h->pop, h->G, h->P, layout, rr, rb, nullptr, h->stream));
+  if (h->ks->compact) {
+    lbm_status st = compact_dens(h);
+    if (st != LBM_OK) return st;
+    LBM_CUDA(h, h->ks->macro_c(h->pop, h->G, h->P, layout, h->dens, rr, rb, nullptr, h->stream));
+  } else {
+    LBM_CUDA(h, h->ks->macro(h->pop, h->G, h->P, layout, rr, rb, nullptr, h->stream));
+  }
   lbmk::k_diag_partial<<<h->diag_blocks, lbmk::DIAG_THREADS, 0, h->stream>>>(
       h->G, h->P.alpha_r, h->P.alpha_b, rr, rb, static_cast<double*>(h->partial));
   LBM_CUDA(h, cudaGetLastError());
@@ -509,6 +577,8 @@ lbm_status lbm_diag(lbm* h, double* mass_rb, double* z_leading_edge, double* dp_
 lbm_status lbm_get_populations(lbm* h, double* f) {
   if (!h) return LBM_EINVAL;
   if (!f) return fail(h, LBM_EINVAL, "f is NULL");
+  if (h->ks->compact && !h->recs_valid)
+    return fail(h, LBM_ESTATE, "compact storage holds the colours of an uploaded state only after its first step");
   const int64_t N = h->N;
   const int layout = (int)(h->t & 1);
   const bool dev = is_device_ptr(f);
@@ -540,7 +610,16 @@ lbm_status lbm_set_populations(lbm* h, const double* f, long long t) {
       inr = h->scratch;
       inb = h->scratch + N;
     }
-    LBM_CUDA(h, h->ks->set_pop(h->pop, h->G, h->P, layout, i, inr, inb, h->stream));
+    if (h->ks->compact)
+      LBM_CUDA(h, h->ks->set_pop_c(h->pop, h->G, h->P, layout, i, inr, inb, h->scratch + 2 * N, h->scratch + 3 * N,
+                                   h->stream));
+    else
+      LBM_CUDA(h, h->ks->set_pop(h->pop, h->G, h->P, layout, i, inr, inb, h->stream));
+  }
+  if (h->ks->compact) {
+    LBM_CUDA(h, h->ks->dens_from_acc(h->G, h->scratch + 2 * N, h->scratch + 3 * N, h->dens, h->stream));
+    h->dens_ready = true;
+    h->recs_valid = false;
   }
   h->t = t;
   h->half = 0;
@@ -550,7 +629,8 @@ lbm_status lbm_set_populations(lbm* h, const double* f, long long t) {
     if (st != LBM_OK) return st;
   }
   LBM_CUDA(h, cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
-  if (h->p.bc[5] == LBM_BC_OUTFLOW) LBM_CUDA(h, h->ks->top_from_state(h->pop, h->G, h->P, layout, h->top, h->stream));
+  if (h->p.bc[5] == LBM_BC_OUTFLOW && !h->ks->compact)
+    LBM_CUDA(h, h->ks->top_from_state(h->pop, h->G, h->P, layout, h->top, h->stream));
   LBM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->unstable = false;
   return LBM_OK;
@@ -561,6 +641,9 @@ lbm_status lbm_profile_step(lbm* h, int n, double* ms_out) {
   if (n < 1 || !ms_out) return fail(h, LBM_EINVAL, "need n >= 1 and an output array of 3 doubles");
   if (h->unstable) return fail(h, LBM_EUNSTABLE, "watchdog: non-finite or non-positive density seen");
   if (h->halo || h->half) return fail(h, LBM_ESTATE, "not available on slab handles or between step passes");
+  if (h->ks->compact && !h->recs_valid)
+    return fail(h, LBM_ESTATE, "compact storage: take one lbm_step after an upload before profiling");
+  if (h->ks->compact) h->dens_ready = false;
   const bool outflow = h->p.bc[5] == LBM_BC_OUTFLOW;
   const int per = 4;
   cudaEvent_t* ev = (cudaEvent_t*)calloc((size_t)per * n, sizeof(cudaEvent_t));
@@ -704,9 +787,12 @@ lbm_status lbm_autotune(lbm* h, int steps, int* chosen) {
   if (steps < 1) return fail(h, LBM_EINVAL, "steps must be >= 1");
   if (h->unstable) return fail(h, LBM_EUNSTABLE, "watchdog: non-finite or non-positive density seen");
   if (h->halo || h->half) return fail(h, LBM_ESTATE, "not available on slab handles or between step passes");
+  if (h->ks->compact && !h->recs_valid)
+    return fail(h, LBM_ESTATE, "compact storage: take one lbm_step after an upload before autotuning");
+  if (h->ks->compact) h->dens_ready = false;
   int cand[4], nc = 0;
   cand[nc++] = 1;
-  if (h->ks->has_paired && h->nx % 2 == 0) cand[nc++] = 2;
+  if (h->ks->has_paired && h->nx % 2 == 0 && !h->ks->compact) cand[nc++] = 2;
   if (h->ks->has_fused) cand[nc++] = 3;
   if (h->ks->has_pipelined) cand[nc++] = 4;
   float ms[4] = {0.f, 0.f, 0.f, 0.f};
@@ -753,6 +839,10 @@ lbm_status lbm_step_pass(lbm* h, int pass) {
   const int layout = (int)(t & 1);
   cudaStream_t s = h->stream;
   if (pass == 1) {
+    if (h->ks->compact && !h->recs_valid) {  // an uploaded state: (rho, phi) is already in dens
+      h->half = 1;
+      return LBM_OK;
+    }
     if (h->variant == 3) {
       lbm_status st = ensure_fix(h, s);
       if (st != LBM_OK) return st;
@@ -771,6 +861,8 @@ lbm_status lbm_step_pass(lbm* h, int pass) {
     LBM_CUDA(h, h->ks->outflow(h->pop, h->G, h->P, layout ^ 1, h->top, fused ? h->fix[layout ^ 1] : nullptr, s));
   h->t += 1;
   h->half = 0;
+  h->recs_valid = true;
+  h->dens_ready = false;
   return LBM_OK;
 }
 
@@ -955,7 +1047,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int n) {
   if (!b || n < 0) return LBM_EINVAL;
   const long long t0 = b->h[0]->t;
   for (lbm* h : b->h) {
-    if (((h->t - t0) & 1) != 0 || h->half) return LBM_ESTATE;
+    if (((h->t - t0) & 1) != 0 || h->half || (h->ks->compact && !h->recs_valid)) return LBM_ESTATE;
     if (h->unstable) return LBM_EUNSTABLE;
   }
   // the batch stream first waits for whatever each handle's own stream has queued ...
@@ -968,6 +1060,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int n) {
   for (lbm* h : b->h) {
     lbm_status st = ensure_fix(h, b->stream);
     if (st != LBM_OK) return st;
+    if (h->ks->compact) h->dens_ready = false;
   }
   int k = 0;
   if (n >= kGraphSteps) {

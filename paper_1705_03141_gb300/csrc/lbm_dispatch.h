@@ -10,6 +10,7 @@ struct Phys;
 struct KernelSet {
   size_t pop_elem_bytes;  // bytes per stored value
   int pop_planes;         // stored planes per direction (2 plain, 1 packed)
+  size_t pop_node_bytes;  // bytes of the population region per storage node (records included)
   size_t dens_bytes;      // bytes per node of the pass-1 field
   size_t real_bytes;      // bytes of the compute type (outflow plane history)
   // pass 1; with fix non-null it writes the fixed-point accumulators of the fused density pass
@@ -36,10 +37,23 @@ struct KernelSet {
   bool has_paired;        // a two-nodes-per-thread pass 2 exists for this storage
   bool has_fused;         // a fused-density pass 2 exists for this storage (FP32 arithmetic)
   bool has_pipelined;     // a software-pipelined pass 2 exists for this storage (packed)
+  // compact storage (per-node colour records): the state after lbm_init_fields / a population
+  // upload has no records, so its first step takes the densities from dens instead of pass 1,
+  // and the I/O kernels below replace init / macro / set_pop
+  bool compact;
+  cudaError_t (*init_c)(void* pop, const Geom& G, const Phys& P, const double* rr, const double* rb,
+                        const double* u, void* dens, cudaStream_t s);
+  cudaError_t (*macro_c)(void* pop, const Geom& G, const Phys& P, int layout, const void* dens, double* rr,
+                         double* rb, double* u, cudaStream_t s);
+  cudaError_t (*set_pop_c)(void* pop, const Geom& G, const Phys& P, int layout, int pdir, const double* in_r,
+                           const double* in_b, double* acc_r, double* acc_b, cudaStream_t s);
+  cudaError_t (*dens_from_acc)(const Geom& G, const double* acc_r, const double* acc_b, void* dens, cudaStream_t s);
 };
 
 const KernelSet* kernels_f64();
 const KernelSet* kernels_f32();
 const KernelSet* kernels_f16();
 const KernelSet* kernels_bf16();
+const KernelSet* kernels_c16();
+const KernelSet* kernels_cbf16();
 }  // namespace lbmk

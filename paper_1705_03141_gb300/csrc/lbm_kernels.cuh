@@ -49,6 +49,8 @@ struct Geom {
   int bc[6];
   int inflow;     // inlet disk active on z = 0
   double xc, yc, r2;
+  float* ctop;    // compact storage with an outflow face: the top plane's populations per colour
+                  // (the outflow history, authoritative for that plane); null otherwise
 };
 
 // Host-side physical parameters (FP64); converted to KConst<R> for the kernels.
@@ -478,6 +480,7 @@ struct Recol {
   R n0, n1, n2;  // unit normal grad(phi)/|grad(phi)| (0 where undefined)
   R rc[4];       // beta rho_r rho_b / rho * varphi_i(alpha_bar) / |c_i| per speed class (rc[0] unused)
   R rho;         // rho of the node (watchdog of the fused density pass)
+  R cr;          // beta rho_r rho_b / rho * (27/19)(1 - alpha_bar): rc[s] = cr w_s / |c| (compact record)
   typename MaskOf<R>::type has_n;
 };
 
@@ -579,6 +582,7 @@ __device__ __forceinline__ Recol<R> collide(const KConst<R>& K, const R rho_r, c
   const R cr = K.beta * rho_r * rho_b * inv_rho * R(27.0 / 19.0) * (R(1) - abar);
   out.frac = rho_r * inv_rho;
   out.rho = rho;
+  out.cr = cr;
   out.rc[0] = R(0);
   out.rc[1] = cr * R(weight_of(tensor_index(1, 0, 0)));
   out.rc[2] = cr * R(weight_of(tensor_index(1, 1, 0)) * 0.70710678118654752440);

@@ -141,10 +141,14 @@ struct Launch {
                                          typename std::conditional<std::is_same<Store, PlainStore<float>>::value, float,
                                                                    uint32_t>::type>::type),
         (std::is_same<Store, PlainStore<double>>::value || std::is_same<Store, PlainStore<float>>::value) ? 2 : 1,
+        (size_t)Store::PLANES * sizeof(typename std::conditional<
+                                    std::is_same<Store, PlainStore<double>>::value, double,
+                                    typename std::conditional<std::is_same<Store, PlainStore<float>>::value,
+                                                              float, uint32_t>::type>::type),
         sizeof(DT),
         sizeof(R),
         &density, &collide, &outflow, &init, &get_pop, &set_pop, &top_from_state, &macro, Tr::paired, fused,
-        pipelined};
+        pipelined, false, nullptr, nullptr, nullptr, nullptr};
     return &ks;
   }
 };

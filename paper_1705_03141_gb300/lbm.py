@@ -15,8 +15,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
 
-STORE_F64, STORE_F32, STORE_F16, STORE_BF16 = range(4)
-STORAGE = {"f64": STORE_F64, "f32": STORE_F32, "f16": STORE_F16, "bf16": STORE_BF16}
+STORE_F64, STORE_F32, STORE_F16, STORE_BF16, STORE_F16C, STORE_BF16C = range(6)
+STORAGE = {"f64": STORE_F64, "f32": STORE_F32, "f16": STORE_F16, "bf16": STORE_BF16, "c16": STORE_F16C,
+           "cbf16": STORE_BF16C}
 BC_PERIODIC, BC_NOSLIP, BC_FREESLIP, BC_INFLOW_WALL, BC_OUTFLOW, BC_HALO = range(6)
 STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA", -4: "LBM_EUNSTABLE",
           -5: "LBM_ETIMEOUT", -6: "LBM_ESTATE"}

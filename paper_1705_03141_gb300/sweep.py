@@ -37,8 +37,8 @@ def run_sweep(n=64, steps=20000, samples=64, seed=2024, storage="f16", tune_step
         lat = lbm.Lattice(w["shape"], w["params"], storage=storage)
         lat.init_fields(rr, rb, u)
         lats.append(lat)
-    for lat in lats:
-        chosen.append(lat.autotune(tune_steps))
+    for lat in lats:  # tune_steps = 0: keep the library's default kernel (reproducible across runs)
+        chosen.append(lat.autotune(tune_steps) if tune_steps > 0 else lat.variant)
     t_tuned = lats[0].time
     batch = lbm.Batch(lats)
     every = max(1, (steps - t_tuned) // samples)

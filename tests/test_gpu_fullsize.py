@@ -63,12 +63,12 @@ def test_fullsize_fp32(cuda, reference):
     assert np.max(np.abs(gu - ou)) < 1e-4 * np.max(np.abs(ou)) + 3e-6 * scale
 
 
-@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("storage", ["f16", "bf16", "c16", "cbf16"])
 def test_fullsize_packed(cuda, reference, storage):
     init, (orr, orb, ou) = reference
     (gr, gb, gu), variant = _run(storage, init)
     assert variant == 1
-    tol = 2e-3 if storage == "f16" else 1e-2
+    tol = 2e-3 if storage in ("f16", "c16") else 1e-2
     scale = max(np.max(np.abs(orr)), np.max(np.abs(orb)))
     assert np.max(np.abs(gr - orr)) < tol * scale
     assert np.max(np.abs(gb - orb)) < tol * scale

@@ -2,8 +2,8 @@
 oracle to 1e-12), on the paper's own set-ups, through the C ABI:
 
   * Laplace pressure of the static droplet (Sec. III.A at the 32^3, R = 8 size, tau = 1,
-    500 steps): FP32 storage within 3e-5 of the FP64 dp, packed half within 2e-3, packed
-    bfloat16 within 3e-2 (relative); every storage keeps sigma from Laplace's law within 10 %
+    500 steps): FP32 storage within 3e-5 of the FP64 dp, half (packed or compact) within 2e-3,
+    bfloat16 (packed or compact) within 3e-2 (relative); every storage keeps sigma from Laplace's law within 10 %
     of Eq. (sigma), the finite-radius error of the FP64 run itself (6-7 % at R = 8);
   * leading edge of a half-scale jet (Sec. IV.A: 64 x 64 x 256, nozzle D = 8, u_j0 = 0.115,
     gamma = 1.2, eta = 3, 2000 steps = 29 D/u_j0, sampled every 500, the tip at 15 D): FP32
@@ -22,8 +22,8 @@ import paper_1705_03141_gb300 as pkg
 
 pytestmark = pytest.mark.gpu
 
-DP_BUDGET = {"f32": 3e-5, "f16": 2e-3, "bf16": 3e-2}
-LE_BUDGET = {"f32": 0.01, "f16": 0.05, "bf16": 0.3}
+DP_BUDGET = {"f32": 3e-5, "f16": 2e-3, "bf16": 3e-2, "c16": 2e-3, "cbf16": 3e-2}
+LE_BUDGET = {"f32": 0.01, "f16": 0.05, "bf16": 0.3, "c16": 0.05, "cbf16": 0.3}
 
 
 def _droplet():
@@ -53,7 +53,7 @@ def laplace64():
     return _laplace("f64")
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16", "c16", "cbf16"])
 def test_laplace_pressure_within_budget(cuda, laplace64, storage):
     dp64, e64, d64 = laplace64
     dp, e, d = _laplace(storage)
@@ -82,7 +82,7 @@ def jet64():
     return _jet_edges("f64")
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16", "c16", "cbf16"])
 def test_jet_leading_edge_within_budget(cuda, jet64, storage):
     z64, D = jet64
     z, _ = _jet_edges(storage)

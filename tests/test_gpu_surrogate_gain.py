@@ -3,11 +3,13 @@
 A batched sweep of 32 jets (the regime-sweep generator: grids 64x64x256 .. 96x96x384, D 8..12,
 log-uniform Re and Oh) runs 4000 steps on the GPU and records each jet's leading edge at 16
 times.  The network (include/lbm_mlp.h) trains on 24 of them; the other 8 are held out, and
-their own simulations decide.  Without the network, a new (Re, Oh, gamma, D) point costs a
+their own simulations decide.  Without the network, a new (Re, Oh, We, gamma, eta) point costs a
 simulation; the best answer that costs nothing is the mean of the simulated trajectories.  The
 test asserts that the network's held-out leading-edge error is below 0.8 of that answer's (the
 FP64 reference network trained the same way on these jets lands at 0.45-0.6 of it, depending
-on the initial weights), and that one query costs less than a millionth of one simulation.
+on the initial weights), and that one query costs less than a millionth of one simulation.  The
+`Surrogate` wrapper answers from the network only inside the trained range and with a confident
+regime; elsewhere the solver runs and answers.
 Kernels and training are bitwise reproducible, so the numbers are fixed for given seeds.
 """
 import numpy as np
@@ -27,18 +29,32 @@ def test_surrogate_beats_the_mean_trajectory_and_the_simulation_cost(cuda):
     res = sweep.run_sweep(n=N_JETS, steps=STEPS, samples=SAMPLES, seed=2024, storage="f16")
     jets = res["jets"]
     assert len(jets) == N_JETS
-    x, t, lab = S.dataset(jets, n_pos=SAMPLES)
-    assert x.shape[0] == N_JETS  # every jet produced the full trajectory
+    x, t, lab, grid = S.dataset(jets, n_pos=SAMPLES)
+    assert x.shape == (N_JETS, S.N_FEATURES)
     xtr, ttr, ltr = x[:N_TRAIN], t[:N_TRAIN], lab[:N_TRAIN]
     xte, tte, lte = x[N_TRAIN:], t[N_TRAIN:], lab[N_TRAIN:]
 
-    net = pkg.Mlp(n_in=5, width=256, depth=4, n_pos=SAMPLES, n_cls=len(L.REGIMES), max_batch=4096, seed=1)
+    net = pkg.Mlp(n_in=S.N_FEATURES, width=256, depth=4, n_pos=SAMPLES, n_cls=len(L.REGIMES), max_batch=4096,
+                  seed=1)
     hist = S.train(net, xtr, ttr, ltr, epochs=1500, lr=1e-3, batch=64)
     held = S.evaluate(net, xte, tte, lte)
     fit = S.evaluate(net, xtr, ttr, ltr)
     mean_traj = ttr.mean(axis=0)
     base = float(np.sqrt(np.mean(((mean_traj[None, :] - tte) * S.Z_SCALE) ** 2)))
     inf = S.time_inference(net, batch=4096, reps=20)
+
+    # the solver as fallback: a training point (inside the box, confidently labelled) gets the
+    # network's answer; a point beyond the trained Re range (outside the box) is simulated, and its
+    # answer is the simulation's own trajectory
+    sur = S.Surrogate(net, xtr, grid, threshold=0.9, samples=SAMPLES)
+    inside = jets[0]["groups"]
+    outside = dict(inside, Re=6e3)
+    a_in, a_out = sur.query([inside, outside])
+    assert a_in["source"] == "network" and a_out["source"] == "solver"
+    np.testing.assert_allclose(a_in["trajectory"], net.forward(xtr[:1])[0, :SAMPLES] * S.Z_SCALE, rtol=1e-6)
+    direct = sur.simulate([outside])[0]  # the same jet simulated again: bitwise reproducible
+    np.testing.assert_array_equal(a_out["trajectory"], direct["trajectory"])
+    assert a_out["trajectory"][-1] > 1.0  # the simulated jet left the nozzle
     net.close()
 
     # seconds of device time one simulated jet costs in this sweep (its share of the batch)

@@ -25,7 +25,8 @@ def test_regime_sweep_ranges():
         assert p["nu_r"] <= 0.015 + 1e-15 and p["A"] <= 0.02 + 1e-15
         assert g["u_j0"] <= 0.1 + 1e-12
         assert math.isclose(g["u_j0"] * g["D"] / p["nu_r"], g["Re"], rel_tol=1e-12)
-        assert math.isclose(p["nu_r"], 3.0 * p["nu_b"], rel_tol=1e-12)
+        assert 1.0 <= g["eta"] <= 5.0  # the viscosity ratio is sampled, so it carries information
+        assert math.isclose(p["nu_r"], g["eta"] * p["nu_b"], rel_tol=1e-12)
         tau = 3.0 * 0.5 * (p["nu_r"] + p["nu_b"]) + 0.5
         sigma = 4.0 / 9.0 * p["A"] * tau
         assert math.isclose(g["We"], g["u_j0"] ** 2 * g["D"] / sigma, rel_tol=1e-12)
@@ -33,4 +34,5 @@ def test_regime_sweep_ranges():
         assert g["regime"] == L.regime_label(g["Re"], g["Oh"], g["We"])
         seen.add(g["regime"])
     assert seen == {0, 1, 2, 3}
+    assert max(w["groups"]["eta"] for w in works) - min(w["groups"]["eta"] for w in works) > 3.0
     assert L.regime_sweep()[7]["params"] == works[7]["params"]  # seeded

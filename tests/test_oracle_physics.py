@@ -482,3 +482,35 @@ def test_free_slip_wall_is_a_mirror_plane():
     for planted in (1, 2):
         p_rho, p_u, _ = _mirror_pair(planted)
         assert p_rho > 1e-6 or p_u > 1e-7, f"ghost_mode {planted} not detected"
+
+
+def test_recolouring_fixes_each_nodes_colour_split_with_four_numbers():
+    """Sec. II: the recolouring hands every population a node emits to the red colour as
+    f^r_i = (rho_r/rho) f*_i + beta (rho_r rho_b/rho^2) cos(theta_i) rho varphi_i(alpha_bar), and
+    varphi_i(alpha) = (27/19)(1 - alpha) w_i for the moving directions, so the red part of every
+    emitted population is frac f*_i + (w_i/|c_i|) c_i . m with one frac = rho_r/rho and one vector
+    m per node (the premise of the compact storage).  Checked on the oracle's own output: in a
+    periodic box the populations node x emits at step t arrive at x + c_i; per node, frac from
+    the rest direction equals rho_r/rho at t, and m fitted to the 26 moving directions leaves a
+    residual at FP64 round-off."""
+    work = L.static_droplet(n=10, R=3.0, rho_r0=1.5)
+    rr, rb, u = L.initial_fields(work, seed=5, u_amp=0.02)
+    o = oracle.Oracle(work["shape"], work["params"])
+    o.init_fields(rr, rb, u)
+    o.step(3)
+    r0, b0, _ = o.macro()
+    o.step(1)
+    f = o.f  # (2, 27, z, y, x) after the step
+    w = oracle.tables()[3]
+    # populations emitted by every node x: the value at x + c_i (periodic)
+    em = np.stack([np.roll(f[:, i], shift=(-C[i][2], -C[i][1], -C[i][0]), axis=(1, 2, 3)) for i in range(27)], axis=1)
+    red, tot = em[0], em[0] + em[1]
+    frac = red[0] / tot[0]
+    np.testing.assert_allclose(frac, r0 / (r0 + b0), rtol=1e-12, atol=1e-14)
+    mov = np.arange(1, 27)
+    A = (w[mov] / np.linalg.norm(C[mov], axis=1))[:, None] * C[mov]  # (26, 3)
+    rhs = (red[mov] - frac[None] * tot[mov]).reshape(26, -1)
+    m, *_ = np.linalg.lstsq(A, rhs, rcond=None)
+    resid = np.abs(A @ m - rhs).max()
+    assert resid < 1e-14 * np.abs(red).max()
+    assert np.abs(m).max() > 1e-4  # the interface carries a real recolouring term
