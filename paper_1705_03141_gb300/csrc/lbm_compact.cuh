@@ -103,42 +103,11 @@ __device__ __forceinline__ float red_of(float f, const float4& r, int j) {
 
 __device__ __forceinline__ bool on_top(const Geom& G, int z) { return G.ctop != nullptr && z == G.nz - 1; }
 
-// record tile: cell (cx, cy, cz) holds the record of node (x0-1+cx, y0-1+cy, z0-1+cz), wrapped
-// across periodic faces; beyond any other face the record of the face node with the normal
-// component of m reversed, which is what a population arriving at the face node from outside
-// carries after the specular reflection of a free-slip wall (Sec. IV.A): it left the face node
-// itself along the mirrored direction.  (Rows that read the tile are fast rows: in y and z they
-// only see cells inside the box, and no-slip x faces exclude them.)
-template <bool BF16>
-__device__ __forceinline__ void fill_record_tile(const CompactStore<BF16>& st, const Geom& G, int x0, int y0,
-                                                 int z0, float4* rt, int tid) {
-  for (int c = tid; c < TILE; c += NTHREADS) {
-    int q[3] = {x0 - 1 + c % TX, y0 - 1 + (c / TX) % TY, z0 - 1 + c / (TX * TY)};
-    const int n[3] = {G.nx, G.ny, G.nz};
-    float sgn[3] = {1.f, 1.f, 1.f};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (q[a] < 0) {
-        if (G.bc[2 * a] == BC_PERIODIC) q[a] += n[a];
-        else { q[a] = 0; sgn[a] = -1.f; }
-      } else if (q[a] >= n[a]) {
-        if (G.bc[2 * a + 1] == BC_PERIODIC && q[a] == n[a]) q[a] = 0;
-        else { q[a] = n[a] - 1; sgn[a] = -1.f; }  // also the unused tail cells of a ragged block
-      }
-    }
-    const float4 r = st.rec[snode(G, q[0], q[1], q[2])];
-    rt[c] = make_float4(r.x, sgn[0] * r.y, sgn[1] * r.z, sgn[2] * r.w);
-  }
-}
-
-// rho and the rebuilt red density of a node on a fast row: direction t arrives in layout 0 in
-// the node's own slot t, in layout 1 in the slot S(x, opp(t)); either way it left node x - c_t
-// along c_t (x faces mirrored in the record tile)
+// loads of the 27 totals of a node on a fast row: direction t in layout 0 from the node's own
+// slot t, in layout 1 from the slot S(x, opp(t))
 template <int LAYOUT, bool BF16>
-__device__ __forceinline__ void fast_red_density(const CompactStore<BF16>& st, const Geom& G, const KConst<float>& K,
-                                                 const AoRow& ar, const float4* rt, int lx, int ly, int lz,
-                                                 float& rho, float& rr) {
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};  // sum of c_t . m(source) per speed class
+__device__ __forceinline__ void fast_totals(const CompactStore<BF16>& st, const Geom& G, const KConst<float>& K,
+                                            const AoRow& ar, float f[27]) {
 #pragma unroll
   for (int t = 0; t < 27; ++t) {
     int64_t e0 = ar.e[1];
@@ -153,53 +122,126 @@ __device__ __forceinline__ void fast_red_density(const CompactStore<BF16>& st, c
 #undef LBMK_CASE
       }
     }
-    const float f = st.load_at(e0, LAYOUT ? opp_of(t) : t, speed2_of(t), K);
-    rho += f;
-    const float4 r = rt[(lx - cx_of(t)) + TX * ((ly - cy_of(t)) + TY * (lz - cz_of(t)))];
-    rr = fmaf(r.x, f, rr);
-    if (t != REST) acc[speed2_of(t)] += cdot_c(t, r.y, r.z, r.w);
+    f[t] = st.load_at(e0, LAYOUT ? opp_of(t) : t, speed2_of(t), K);
   }
-#pragma unroll
-  for (int s = 1; s < 4; ++s) rr = fmaf(split_coef(s), acc[s], rr);
 }
 
-// pass 1 (compact): rho and the rebuilt red density of every node -> (rho, phi)
+// one coordinate of a record tile cell: wrapped across a periodic face, else clamped, with the
+// sign that the component of m along that axis takes in the mirror image (-1 beyond the face)
+__device__ __forceinline__ int tile_coord(int q, int n, int bc_lo, int bc_hi, float& sgn) {
+  sgn = 1.f;
+  if (q < 0) {
+    if (bc_lo == BC_PERIODIC) return q + n;
+    sgn = -1.f;
+    return 0;
+  }
+  if (q >= n) {
+    if (bc_hi == BC_PERIODIC && q == n) return 0;
+    sgn = -1.f;
+    return n - 1;  // also the unused tail cells of a ragged block
+  }
+  return q;
+}
+
+// record tile: cell (cx, cy, cz) holds the record of node (x0-1+cx, y0-1+cy, z0-1+cz), wrapped
+// across periodic faces; beyond any other face the record of the face node with the normal
+// component of m reversed, which is what a population arriving at the face node from outside
+// carries after the specular reflection of a free-slip wall (Sec. IV.A): it left the face node
+// itself along the mirrored direction.  (Rows that read the tile are fast rows: in y and z they
+// only see cells inside the box, and no-slip x faces exclude them.)  Warp w fills tile rows w,
+// w + 8, w + 16; lanes take the columns, lanes 0 and 1 also columns 32 and 33.
 template <bool BF16>
-__global__ void __launch_bounds__(NTHREADS, 2) k_density_c(CompactStore<BF16> st, const __grid_constant__ Geom G,
-                                                        const __grid_constant__ KConst<float> K, int layout,
-                                                        float2* __restrict__ dens, int* __restrict__ flag) {
+__device__ __forceinline__ void fill_record_tile(const CompactStore<BF16>& st, const Geom& G, int x0, int y0,
+                                                 int z0, float4* rt, int tid) {
+  const int warp = tid >> 5, lane = tid & 31;
+  float sa, sb;
+  const int xa = tile_coord(x0 - 1 + lane, G.nx, G.bc[0], G.bc[1], sa);
+  const int xb = tile_coord(x0 + 31 + lane, G.nx, G.bc[0], G.bc[1], sb);
+#pragma unroll
+  for (int k = 0; k < (TY * TZ + NWARPS - 1) / NWARPS; ++k) {
+    const int row = warp + k * NWARPS;
+    if (row < TY * TZ) {
+      float sy, sz;
+      const int gy = tile_coord(y0 - 1 + row % TY, G.ny, G.bc[2], G.bc[3], sy);
+      const int gz = tile_coord(z0 - 1 + row / TY, G.nz, G.bc[4], G.bc[5], sz);
+      const float4* rrow = st.rec + snode(G, 0, gy, gz);
+      const float4 a = rrow[xa];
+      rt[row * TX + lane] = make_float4(a.x, sa * a.y, sy * a.z, sz * a.w);
+      if (lane < TX - 32) {
+        const float4 b = rrow[xb];
+        rt[row * TX + 32 + lane] = make_float4(b.x, sb * b.y, sy * b.z, sz * b.w);
+      }
+    }
+  }
+}
+
+// pass 1 (compact): rho and the rebuilt red density of every node -> (rho, phi).  The totals are
+// loaded first and the record tile filled while they arrive; on a fast row the value arriving
+// along c_t left node x - c_t along c_t (x faces mirrored in the tile), elsewhere the emitter is
+// the owner of S(x, opp(t)) and its direction opp(stored direction) (records read directly)
+template <bool BF16>
+__global__ void __launch_bounds__(NTHREADS, 3) k_density_c(CompactStore<BF16> st, const __grid_constant__ Geom G,
+                                                           const __grid_constant__ KConst<float> K, int layout,
+                                                           float2* __restrict__ dens, int* __restrict__ flag) {
   __shared__ float4 rt[TILE];
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * BZ;
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
   const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
+  const bool active = x < G.nx && y < G.ny && z < G.nz;
+  const bool top = on_top(G, z);
+  const bool fast = !top && fast_row(G, y, z);
+  float f[27];
+  if (active && !top) {
+    if (fast) {
+      AoRow ar;
+      ar.init<CPLANES>(G, x, y, z);
+      if (!layout) fast_totals<0>(st, G, K, ar, f);
+      else fast_totals<1>(st, G, K, ar, f);
+    } else {
+      NodeMap nm;
+      nm.init(G, x, y, z);
+#pragma unroll
+      for (int t = 0; t < 27; ++t) {
+        int64_t node;
+        int dir;
+        slot_of(nm, layout, t, node, dir);
+        f[t] = st.load(node, dir, speed2_of(t), K);
+      }
+    }
+  }
   fill_record_tile(st, G, x0, y0, z0, rt, tid);
   __syncthreads();
-  if (x >= G.nx || y >= G.ny || z >= G.nz) return;
+  if (!active) return;
   float rho = 0.f, rr = 0.f;
-  if (on_top(G, z)) {
+  if (top) {
     const float* tp = G.ctop + ((int64_t)x + (int64_t)G.nx * y) * 64;
 #pragma unroll
     for (int t = 0; t < 27; ++t) {
       rr += tp[t];
       rho += tp[t] + tp[32 + t];
     }
-  } else if (fast_row(G, y, z)) {
-    AoRow ar;
-    ar.init<CPLANES>(G, x, y, z);
+  } else if (fast) {
     const int lx = threadIdx.x + 1, ly = threadIdx.y + 1, lz = threadIdx.z + 1;
-    if (!layout) fast_red_density<0>(st, G, K, ar, rt, lx, ly, lz, rho, rr);
-    else fast_red_density<1>(st, G, K, ar, rt, lx, ly, lz, rho, rr);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};  // sum of c_t . m(emitter) per speed class
+#pragma unroll
+    for (int t = 0; t < 27; ++t) {
+      rho += f[t];
+      const float4 r = rt[(lx - cx_of(t)) + TX * ((ly - cy_of(t)) + TY * (lz - cz_of(t)))];
+      rr = fmaf(r.x, f[t], rr);
+      if (t != REST) acc[speed2_of(t)] += cdot_c(t, r.y, r.z, r.w);
+    }
+#pragma unroll
+    for (int s = 1; s < 4; ++s) rr = fmaf(split_coef(s), acc[s], rr);
   } else {
     NodeMap nm;
     nm.init(G, x, y, z);
+#pragma unroll
     for (int t = 0; t < 27; ++t) {
-      int64_t node, src;
-      int dir, sdir;
-      slot_of(nm, layout, t, node, dir);
+      int64_t src;
+      int sdir;
       slot_of(nm, 1, t, src, sdir);  // S(x, opp(t)): its owner emitted the value, along opp(sdir)
-      const float f = st.load(node, dir, speed2_of(t), K);
-      rho += f;
-      rr += red_of(f, st.rec[src], opp_of(sdir));
+      rho += f[t];
+      rr += red_of(f[t], st.rec[src], opp_of(sdir));
     }
   }
   if (!(rho > 0.f) || !(rho < 1e30f)) atomicOr(flag, 1);
@@ -317,11 +359,12 @@ __global__ void __launch_bounds__(NTHREADS, 4)
   if (fast) {
     AoRow ar;
     ar.init<CPLANES>(G, x, y, z);
+    if (!odd) {
 #pragma unroll
-    for (int t = 0; t < 27; ++t) {
-      if (!odd) {
-        st.store_at(ar.e[1], opp_of(t), speed2_of(t), K, f[t]);
-      } else {
+      for (int t = 0; t < 27; ++t) st.store_at(ar.e[1], opp_of(t), speed2_of(t), K, f[t]);
+    } else {
+#pragma unroll
+      for (int t = 0; t < 27; ++t) {
         int64_t e0;
         switch (t) {
 #define LBMK_CASE(k) case k: e0 = ar.slot0<k, CPLANES>(G); break;

@@ -1,8 +1,8 @@
 """What the trained surrogate gains over the solver alone (the regime-map use of Sec. IV.C).
 
 A batched sweep of 32 jets (the regime-sweep generator: grids 64x64x256 .. 96x96x384, D 8..12,
-log-uniform Re and Oh) runs 4000 steps on the GPU and records each jet's leading edge at 16
-times.  The network (include/lbm_mlp.h) trains on 24 of them; the other 8 are held out, and
+log-uniform Re and Oh, eta in [1, 5]) runs 8000 steps on the GPU and records each jet's leading
+edge at 16 common times t* = t u_j0/D (up to the last time the slowest jet reached).  The network (include/lbm_mlp.h) trains on 24 of them; the other 8 are held out, and
 their own simulations decide.  Without the network, a new (Re, Oh, We, gamma, eta) point costs a
 simulation; the best answer that costs nothing is the mean of the simulated trajectories.  The
 test asserts that the network's held-out leading-edge error is below 0.8 of that answer's (the
@@ -22,7 +22,7 @@ from paper_1705_03141_gb300 import sweep
 
 pytestmark = pytest.mark.gpu
 
-N_JETS, N_TRAIN, STEPS, SAMPLES = 32, 24, 4000, 16
+N_JETS, N_TRAIN, STEPS, SAMPLES = 32, 24, 8000, 16
 
 
 def test_surrogate_beats_the_mean_trajectory_and_the_simulation_cost(cuda):
