@@ -274,6 +274,21 @@ struct PlainStore {  // FP64 or FP32: f^r and f^b planes [2][27][Ns]
     fr = (R)__ldcs(A + e0 + dir * 32);
     ft = fr + (R)__ldcs(A + e0 + (27 + dir) * 32);
   }
+  // loads that add the red population to acc (red_finish(acc) is the red density)
+  template <typename R>
+  __device__ __forceinline__ void load_red_at(int64_t e0, int dir, int cls, const KConst<R>& K, R& acc, R& ft) const {
+    R fr;
+    load_at(e0, dir, cls, K, fr, ft);
+    acc += fr;
+  }
+  template <typename R>
+  __device__ __forceinline__ void load_red(int64_t node, int dir, int cls, const KConst<R>& K, R& acc, R& ft) const {
+    R fr;
+    load(node, dir, cls, K, fr, ft);
+    acc += fr;
+  }
+  template <typename R>
+  __device__ __forceinline__ static R red_finish(R acc) { return acc; }
   template <typename R>
   __device__ __forceinline__ void store_at(int64_t e0, int dir, int, const KConst<R>&, R outr, R outb, R, R) const {
     __stcs(A + e0 + dir * 32, (T)outr);
@@ -369,6 +384,26 @@ struct PackedStore {
                                            R q) const {
     __stcs(A + e0 + dir * 32, encode((float)K.refB[cls], cls == 0 ? (float)K.dref[0] : 0.0f, (float)fstar, (float)q));
   }
+  // loads that add code(q) * f to acc: the red density is (1/65535) sum_i code_i f_i
+  // (red_finish), one multiply per node instead of one per direction
+  __device__ __forceinline__ static float decode_red(uint32_t w, float rB, float dR, float& acc) {
+    const float k = code_to_float(w >> 16);
+    const float f = (dR != 0.0f ? fmaf(k * (1.0f / 65535.0f), dR, rB) : rB) + dev_to_float(w);
+    acc = fmaf(k, f, acc);
+    return f;
+  }
+  template <typename R>
+  __device__ __forceinline__ void load_red_at(int64_t e0, int dir, int cls, const KConst<R>& K, R& acc, R& ft) const {
+    float a = (float)acc;
+    ft = (R)decode_red(__ldcs(A + e0 + dir * 32), (float)K.refB[cls], cls == 0 ? (float)K.dref[0] : 0.0f, a);
+    acc = (R)a;
+  }
+  template <typename R>
+  __device__ __forceinline__ void load_red(int64_t node, int dir, int cls, const KConst<R>& K, R& acc, R& ft) const {
+    load_red_at(elem_index(node, PLANES, 0), dir, cls, K, acc, ft);
+  }
+  template <typename R>
+  __device__ __forceinline__ static R red_finish(R acc) { return acc * R(1.0 / 65535.0); }
   template <typename R>
   __device__ __forceinline__ void load_rb(int64_t node, int dir, int cls, const KConst<R>& K, R& fr, R& fb) const {
     R ft;
@@ -410,24 +445,20 @@ struct DensOf<PlainStore<double>> { using type = double2; using real = double; }
 template <class Store, typename R>
 __device__ __forceinline__ void load_node(const Store& st, const KConst<R>& K, const NodeMap& nm, int layout,
                                           R& rho_r, R ft[27]) {
+  R acc = R(0);
   if (layout == 0) {
 #pragma unroll
-    for (int t = 0; t < 27; ++t) {
-      R fr;
-      st.load(nm.base, t, speed2_of(t), K, fr, ft[t]);
-      rho_r += fr;
-    }
+    for (int t = 0; t < 27; ++t) st.load_red(nm.base, t, speed2_of(t), K, acc, ft[t]);
   } else {
 #pragma unroll
     for (int t = 0; t < 27; ++t) {
       int64_t node;
       int dir;
       slot_of(nm, 1, t, node, dir);
-      R fr;
-      st.load(node, dir, speed2_of(t), K, fr, ft[t]);
-      rho_r += fr;
+      st.load_red(node, dir, speed2_of(t), K, acc, ft[t]);
     }
   }
+  rho_r += Store::red_finish(acc);
 }
 
 // loads of a node on a fast row: even steps read plane t of the node itself,
@@ -435,13 +466,10 @@ __device__ __forceinline__ void load_node(const Store& st, const KConst<R>& K, c
 template <class Store, typename R>
 __device__ __forceinline__ void load_node_fast(const Store& st, const KConst<R>& K, const Geom& G, const AoRow& ar,
                                                int odd, R& rho_r, R ft[27]) {
+  R acc = R(0);
   if (!odd) {
 #pragma unroll
-    for (int t = 0; t < 27; ++t) {
-      R fr;
-      st.load_at(ar.e[1], t, speed2_of(t), K, fr, ft[t]);
-      rho_r += fr;
-    }
+    for (int t = 0; t < 27; ++t) st.load_red_at(ar.e[1], t, speed2_of(t), K, acc, ft[t]);
   } else {
 #pragma unroll
     for (int t = 0; t < 27; ++t) {
@@ -455,11 +483,10 @@ __device__ __forceinline__ void load_node_fast(const Store& st, const KConst<R>&
         default: e0 = ar.slot0<26, Store::PLANES>(G); break;
 #undef LBMK_CASE
       }
-      R fr;
-      st.load_at(e0, opp_of(t), speed2_of(t), K, fr, ft[t]);
-      rho_r += fr;
+      st.load_red_at(e0, opp_of(t), speed2_of(t), K, acc, ft[t]);
     }
   }
+  rho_r += Store::red_finish(acc);
 }
 
 // body force (Eq. Momentum / Eq. ketFd)
@@ -811,9 +838,11 @@ __device__ __forceinline__ void tile_gradients(const DT* tile, int lx, int ly, i
 // write direction T of the node (step parity `odd`): colours, f* and red fraction.
 // RECOL: some node of the warp has an interface normal (otherwise the
 // recolouring term is zero and the red fraction of every direction is rho_r/rho).
-template <int T, bool FAST, bool RECOL, class Store, typename R>
+// ODDT: the step parity at compile time (0 or 1), or -1 to take it from `odd`
+template <int T, bool FAST, bool RECOL, int ODDT, class Store, typename R>
 __device__ __forceinline__ void emit(const Store& st, const KConst<R>& K, const Geom& G, const NodeMap& nm,
-                                     const AoRow& ar, bool odd, const R f[27], const Recol<R>& rc) {
+                                     const AoRow& ar, bool odd_rt, const R f[27], const Recol<R>& rc) {
+  const bool odd = ODDT < 0 ? odd_rt : ODDT != 0;
   const R fstar = f[T];
   R outr, q;
   if (T == REST || !RECOL) {
@@ -840,12 +869,12 @@ __device__ __forceinline__ void emit(const Store& st, const KConst<R>& K, const 
 
 // FUSED: after each direction (fast rows: each triple of directions), add it to the
 // next step's densities (fused density pass; prow, io as in k_collide_stream)
-template <int T, class Store, typename R, bool FAST, bool RECOL, bool FUSED>
+template <int T, class Store, typename R, bool FAST, bool RECOL, bool FUSED, int ODDT = -1>
 struct EmitLoop {
   __device__ __forceinline__ static void run(const Store& st, const KConst<R>& K, const Geom& G, const NodeMap& nm,
                                              const AoRow& ar, bool odd, const R* f, const Recol<R>& rc,
                                              float2* prow, const FusedIO& io, int x, int y, int z) {
-    emit<T, FAST, RECOL>(st, K, G, nm, ar, odd, f, rc);
+    emit<T, FAST, RECOL, ODDT>(st, K, G, nm, ar, odd, f, rc);
     if constexpr (FUSED) {
       if constexpr (FAST) {
         if constexpr (T % 3 == 2) fused_row<T / 3, RECOL>(prow, f, rc);
@@ -853,11 +882,11 @@ struct EmitLoop {
         fused_node<T>(G, io, x, y, z, f, rc);
       }
     }
-    EmitLoop<T + 1, Store, R, FAST, RECOL, FUSED>::run(st, K, G, nm, ar, odd, f, rc, prow, io, x, y, z);
+    EmitLoop<T + 1, Store, R, FAST, RECOL, FUSED, ODDT>::run(st, K, G, nm, ar, odd, f, rc, prow, io, x, y, z);
   }
 };
-template <class Store, typename R, bool FAST, bool RECOL, bool FUSED>
-struct EmitLoop<27, Store, R, FAST, RECOL, FUSED> {
+template <class Store, typename R, bool FAST, bool RECOL, bool FUSED, int ODDT>
+struct EmitLoop<27, Store, R, FAST, RECOL, FUSED, ODDT> {
   __device__ __forceinline__ static void run(const Store&, const KConst<R>&, const Geom&, const NodeMap&,
                                              const AoRow&, bool, const R*, const Recol<R>&, float2*, const FusedIO&,
                                              int, int, int) {}
@@ -1023,8 +1052,18 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
     AoRow ar;
     if (fast) {
       ar.init<Store::PLANES>(G, x, y, z);
-      if (recol) EmitLoop<0, Store, R, true, true, FUSED>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
-      else EmitLoop<0, Store, R, true, false, FUSED>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
+      // the parity as a template argument: no per-direction branch on it in the stores (the
+      // fused density pass keeps it a runtime value: the extra code raised its spills)
+      if constexpr (FUSED) {
+        if (recol) EmitLoop<0, Store, R, true, true, FUSED>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
+        else EmitLoop<0, Store, R, true, false, FUSED>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
+      } else if (recol) {
+        if (odd) EmitLoop<0, Store, R, true, true, FUSED, 1>::run(st, K, G, nm, ar, true, f, rc, prow, io, x, y, z);
+        else EmitLoop<0, Store, R, true, true, FUSED, 0>::run(st, K, G, nm, ar, false, f, rc, prow, io, x, y, z);
+      } else {
+        if (odd) EmitLoop<0, Store, R, true, false, FUSED, 1>::run(st, K, G, nm, ar, true, f, rc, prow, io, x, y, z);
+        else EmitLoop<0, Store, R, true, false, FUSED, 0>::run(st, K, G, nm, ar, false, f, rc, prow, io, x, y, z);
+      }
     } else {
       if (odd) nm.init(G, x, y, z);
       else nm.base = snode(G, x, y, z);  // the even step only uses the base
