@@ -52,6 +52,7 @@ UNIT = "MLUPS"
 POP_BYTES = {"f64": 8 * 54, "f32": 4 * 54, "f16": 4 * 27, "bf16": 4 * 27, "c16": 56, "cbf16": 56}
 DENS_BYTES = {"f64": 16, "f32": 8, "f16": 8, "bf16": 8, "c16": 8, "cbf16": 8}
 RECORD_BYTES = {"c16": 16, "cbf16": 16}
+BLOCKS = {1: "32x4x2", 2: "32x2x4", 3: "32x8x1"}
 
 
 def workload(seed=1234):
@@ -337,7 +338,7 @@ def end_to_end(pkg, torch, w, rr, rb, u, args, ws, dev):
     out = (torch.empty(rr.shape, dtype=torch.float64).pin_memory(),
            torch.empty(rb.shape, dtype=torch.float64).pin_memory(),
            torch.empty(u.shape, dtype=torch.float64).pin_memory())
-    late = pkg.Lattice(shape, w["params"], storage=args.storage, variant=args.variant)
+    late = pkg.Lattice(shape, w["params"], storage=args.storage, variant=args.variant, block=args.block)
     late.init_fields(hr, hb, hu)
     late.step(args.warmup)
     late.synchronize()
@@ -380,6 +381,8 @@ def main():
                     help="also time the oracle on the droplet set-ups and a jet sample, 1 and all threads")
     ap.add_argument("--variant", type=int, default=0, help="collide-stream kernel: 0 library choice, 1 one node "
                     "per thread, 2 two nodes per thread, 3 fused density pass, 4 software-pipelined (packed)")
+    ap.add_argument("--block", type=int, default=0, help="block shape of the one-node kernels: 0 library choice, "
+                    "1 32x4x2, 2 32x2x4, 3 32x8x1")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -407,7 +410,7 @@ def main():
     rr, rb, u = L.initial_fields(w)
 
     def make(storage):
-        lat = pkg.Lattice(shape, w["params"], storage=storage, variant=args.variant)
+        lat = pkg.Lattice(shape, w["params"], storage=storage, variant=args.variant, block=args.block)
         lat.init_fields(rr, rb, u)
         return lat
 
@@ -434,6 +437,7 @@ def main():
     mlups = ws * N * args.steps / dt_max / 1e6
     kps = lat.kernels_per_step
     variant = lat.variant
+    block = lat.block
     # live per-kernel timing of the same configuration (CUDA events on the kernels' stream)
     ms = lat.profile_step(min(200, args.steps))
     lat.close()
@@ -445,11 +449,12 @@ def main():
         lat32.step(args.warmup)
         dt32 = max_over_ranks(timed(lat32, args.steps), ws, dev)
         variant32 = lat32.variant
+        block32 = lat32.block
         ms32 = lat32.profile_step(min(200, args.steps))
         lat32.close()
         bytes32 = N * collide_bytes("f32", variant32)
         fp32 = {"value": ws * N * args.steps / dt32 / 1e6, "ms_per_step": dt32 / args.steps * 1e3,
-                "variant": variant32, "pass1_ms": ms32[0], "collide_ms": ms32[1],
+                "variant": variant32, "block": BLOCKS[block32], "pass1_ms": ms32[0], "collide_ms": ms32[1],
                 "collide_gbs": bytes32 / (ms32[1] * 1e-3) / 1e9, "collide_bytes_per_node": bytes32 // N,
                 "collide_traffic": profiled_traffic("f32", variant32)}
 
@@ -469,7 +474,7 @@ def main():
             "frac": achieved / peak, "peak_kind": peak_kind, "frac_of_nominal_7900": achieved / 7900.0,
             "traffic": traffic,
             "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": ms[1],
-            "variant": variant, "density_pass_ms": ms[0], "outflow_ms": ms[2],
+            "variant": variant, "block": BLOCKS[block], "density_pass_ms": ms[0], "outflow_ms": ms[2],
             "step_share_collide": ms[1] / max(sum(ms), 1e-12),
             "alu": alu_roof(pkg, args.storage, N, ms[1], fp32_peak, variant)}
     if fp32 is not None:

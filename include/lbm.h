@@ -160,6 +160,16 @@ typedef struct {
                             densities that enter the gradients to fixed point), and
                             each is bitwise reproducible.  F32/F16/BF16 storage needs
                             rho_r0, rho_b0 <= 64. */
+  int block;             /* thread-block shape of the one-node density and
+                            collide-stream kernels (variants 1 and 3, FP32
+                            arithmetic): 0 = library's choice (32x2x4 for variant 3
+                            in F32 storage, else 32x4x2: the measured faster ones),
+                            1 = 32x4x2 nodes, 2 = 32x2x4, 3 = 32x8x1 (a warp is one
+                            32-node x-row in each).  Variant 1 computes the same
+                            update bitwise in every shape; variant 3 differs by FP32
+                            rounding (how the next step's densities are grouped
+                            before their exact fixed-point sum).  FP64 and compact
+                            storage always run 32x4x2. */
 } lbm_params;
 
 typedef struct lbm lbm; /* opaque handle; owns all device state it allocated */
@@ -244,6 +254,11 @@ LBM_EXPORT int lbm_kernels_per_step(const lbm* h);
  * lbm_params.variant and lbm_autotune); -1 for NULL. */
 LBM_EXPORT int lbm_kernel_variant(const lbm* h);
 
+/* The block shape the handle's one-node kernels run (1 = 32x4x2, 2 = 32x2x4,
+ * 3 = 32x8x1: lbm_params.block, the library's choice, or the one lbm_autotune
+ * chose); -1 for NULL. */
+LBM_EXPORT int lbm_kernel_block(const lbm* h);
+
 /* Last error message of this handle ("" if none); valid until the next call. */
 LBM_EXPORT const char* lbm_last_error(const lbm* h);
 
@@ -262,11 +277,13 @@ LBM_EXPORT lbm_status lbm_selfcheck(const char** msg);
 
 /* Pick the fastest collide-stream kernel for this handle by measurement: take
  * `steps` steps (>= 1) with each available variant (1; 2 where the storage and
- * nx allow; 3 for F32/F16/BF16 storage; 4 for F16/BF16 storage), timed with
- * CUDA events on the handle's stream, keep the fastest for later steps and
- * report it in *chosen (1 to 4; may be NULL).  The tuning steps are ordinary
- * time steps of the same update, so the time advances by steps times the
- * number of variants tried.  Synchronises. */
+ * nx allow; 3 for F32/F16/BF16 storage; 4 for F16/BF16 storage), variants 1
+ * and 3 in each of the three block shapes of lbm_params.block (FP32-arithmetic
+ * storages other than compact), timed with CUDA events on the handle's stream,
+ * keep the fastest (variant, shape) for later steps and report the variant in
+ * *chosen (1 to 4; may be NULL; lbm_kernel_block gives the shape).  The tuning
+ * steps are ordinary time steps of the same update, so the time advances by
+ * steps times the number of candidates tried.  Synchronises. */
 LBM_EXPORT lbm_status lbm_autotune(lbm* h, int steps, int* chosen);
 
 /* Batched stepping of several independent boxes (e.g. the jets of a regime

@@ -48,6 +48,7 @@ struct lbm {
   double *diag_out, *scratch;
   int diag_blocks;
   int variant;  // pass-2 kernel: 1 = one node per thread, 2 = two nodes per thread, 3 = fused density
+  int shape;    // block shape of the one-node kernels (lbm_params.block)
   cudaStream_t stream;
   cudaStream_t cap_stream;
   cudaGraphExec_t graph[2];  // kGraphSteps steps starting at an even / odd step
@@ -123,6 +124,7 @@ const char* validate(int nx, int ny, int nz, const lbm_params* p) {
     if (p->bc[f] == LBM_BC_OUTFLOW && f != 5) return "OUTFLOW is only allowed on the +z face";
   }
   if (p->storage < 0 || p->storage > 5) return "unknown storage";
+  if (p->block < 0 || p->block > 3) return "unknown block shape (0: library's choice, 1: 32x4x2, 2: 32x2x4, 3: 32x8x1)";
   if (p->storage == LBM_STORE_F16C || p->storage == LBM_STORE_BF16C) {
     if (p->variant > 1) return "compact storage runs the one-node collide-stream kernel (variant 0 or 1)";
     if (p->bc[4] == LBM_BC_HALO || p->bc[5] == LBM_BC_HALO) return "compact storage has no z-slab halo exchange";
@@ -204,14 +206,14 @@ lbm_status enqueue_step(lbm* h, long long t, cudaStream_t s, bool skip_density =
     // fused density pass: no pass 1; the accumulators of t+1 start from zero
     unsigned long long *cur = h->fix[layout], *nxt = h->fix[layout ^ 1];
     LBM_CUDA(h, cudaMemsetAsync(nxt, 0, sizeof(unsigned long long) * (size_t)h->N, s));
-    LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, 3, cur, nxt, h->flag, s));
+    LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, 3, cur, nxt, h->flag, h->shape, s));
     if (outflow) LBM_CUDA(h, h->ks->outflow(h->pop, h->G, h->P, layout ^ 1, h->top, nxt, s));
     return LBM_OK;
   }
   h->fix_ready = false;  // steps without the fused pass leave its accumulators behind
-  if (!skip_density) LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, nullptr, s));
+  if (!skip_density) LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, nullptr, h->shape, s));
   LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->variant, nullptr, nullptr,
-                             h->flag, s));
+                             h->flag, h->shape, s));
   if (outflow) LBM_CUDA(h, h->ks->outflow(h->pop, h->G, h->P, layout ^ 1, h->top, nullptr, s));
   return LBM_OK;
 }
@@ -219,7 +221,7 @@ lbm_status enqueue_step(lbm* h, long long t, cudaStream_t s, bool skip_density =
 // before fused steps from a state the fused pass did not produce: fill the accumulators of step t
 lbm_status ensure_fix(lbm* h, cudaStream_t s) {
   if (h->variant != 3 || h->fix_ready) return LBM_OK;
-  LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, (int)(h->t & 1), h->dens, h->flag, h->fix[h->t & 1], s));
+  LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, (int)(h->t & 1), h->dens, h->flag, h->fix[h->t & 1], h->shape, s));
   h->fix_ready = true;
   return LBM_OK;
 }
@@ -265,7 +267,7 @@ lbm_status compact_first_step(lbm* h, cudaStream_t s) {
 // compact storage: (rho, phi) of the current state in dens (pass 1, if not already there)
 lbm_status compact_dens(lbm* h) {
   if (!h->ks->compact || h->dens_ready) return LBM_OK;
-  LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, (int)(h->t & 1), h->dens, h->flag, nullptr, h->stream));
+  LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, (int)(h->t & 1), h->dens, h->flag, nullptr, h->shape, h->stream));
   h->dens_ready = true;
   return LBM_OK;
 }
@@ -331,6 +333,9 @@ lbm_status lbm_create(int nx, int ny, int nz, const lbm_params* p, lbm** out) {
   h->variant = p->variant != 0 ? p->variant
                                : (p->storage == LBM_STORE_F32 && nx % 32 == 0 && !h->halo ? 3 : 1);
   h->fix_ready = false;
+  // block shape: as measured on GB300 (128x128x512 jet), the fused FP32 kernel runs fastest in
+  // 32x2x4 blocks (0.784 against 0.814 ms for 32x4x2); every other kernel in 32x4x2
+  h->shape = p->block != 0 ? p->block - 1 : (h->variant == 3 && p->storage == LBM_STORE_F32 ? 1 : 0);
 
   Geom& G = h->G;
   G.nx = nx;
@@ -669,11 +674,11 @@ lbm_status lbm_profile_step(lbm* h, int n, double* ms_out) {
     const size_t nfix = sizeof(unsigned long long) * (size_t)h->N;
     if (cudaEventRecord(e[0], h->stream) != cudaSuccess ||
         (fused ? cudaMemsetAsync(nxt, 0, nfix, h->stream)
-               : h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, nullptr, h->stream)) !=
+               : h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, nullptr, h->shape, h->stream)) !=
             cudaSuccess ||
         cudaEventRecord(e[1], h->stream) != cudaSuccess ||
         h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->variant, fused ? cur : nullptr,
-                       fused ? nxt : nullptr, h->flag, h->stream) != cudaSuccess ||
+                       fused ? nxt : nullptr, h->flag, h->shape, h->stream) != cudaSuccess ||
         cudaEventRecord(e[2], h->stream) != cudaSuccess ||
         (outflow && h->ks->outflow(h->pop, h->G, h->P, layout ^ 1, h->top, fused ? nxt : nullptr, h->stream) !=
                         cudaSuccess) ||
@@ -722,6 +727,8 @@ int lbm_kernels_per_step(const lbm* h) {
 }
 
 int lbm_kernel_variant(const lbm* h) { return h ? h->variant : -1; }
+
+int lbm_kernel_block(const lbm* h) { return h ? h->shape + 1 : -1; }
 
 const char* lbm_last_error(const lbm* h) { return h ? h->err.c_str() : "NULL handle"; }
 
@@ -790,12 +797,21 @@ lbm_status lbm_autotune(lbm* h, int steps, int* chosen) {
   if (h->ks->compact && !h->recs_valid)
     return fail(h, LBM_ESTATE, "compact storage: take one lbm_step after an upload before autotuning");
   if (h->ks->compact) h->dens_ready = false;
-  int cand[4], nc = 0;
-  cand[nc++] = 1;
-  if (h->ks->has_paired && h->nx % 2 == 0 && !h->ks->compact) cand[nc++] = 2;
-  if (h->ks->has_fused) cand[nc++] = 3;
-  if (h->ks->has_pipelined) cand[nc++] = 4;
-  float ms[4] = {0.f, 0.f, 0.f, 0.f};
+  // candidates: (variant, block shape); the shapes apply to the one-node kernels (variants 1, 3)
+  // of the FP32-arithmetic storages
+  int cand[12][2], nc = 0;
+  const bool shapes = !h->ks->compact && h->p.storage != LBM_STORE_F64;
+  for (int v = 1; v <= 4; ++v) {
+    if (v == 2 && !(h->ks->has_paired && h->nx % 2 == 0 && !h->ks->compact)) continue;
+    if (v == 3 && !h->ks->has_fused) continue;
+    if (v == 4 && !h->ks->has_pipelined) continue;
+    for (int b = 0; b < ((v == 1 || v == 3) && shapes ? 3 : 1); ++b) {
+      cand[nc][0] = v;
+      cand[nc][1] = b;
+      ++nc;
+    }
+  }
+  float ms[12] = {0.f};
   cudaEvent_t e0, e1;
   LBM_CUDA(h, cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -804,7 +820,9 @@ lbm_status lbm_autotune(lbm* h, int steps, int* chosen) {
   }
   lbm_status st = LBM_OK;
   for (int c = 0; c < nc && st == LBM_OK; ++c) {
-    h->variant = cand[c];
+    if (h->variant != cand[c][0]) h->fix_ready = false;
+    h->variant = cand[c][0];
+    h->shape = cand[c][1];
     st = ensure_fix(h, h->stream);  // untimed: only needed when entering the fused pass
     // direct launches: every kernel timed the same way, no graph capture in between
     if (st == LBM_OK && cudaEventRecord(e0, h->stream) != cudaSuccess)
@@ -823,8 +841,9 @@ lbm_status lbm_autotune(lbm* h, int steps, int* chosen) {
   int best = 0;
   for (int c = 1; c < nc; ++c)
     if (ms[c] < ms[best]) best = c;
-  if (h->variant != cand[best]) h->fix_ready = false;
-  h->variant = cand[best];
+  if (h->variant != cand[best][0]) h->fix_ready = false;
+  h->variant = cand[best][0];
+  h->shape = cand[best][1];
   drop_graphs(h);  // captured graphs hold the kernel of the previous choice
   if (chosen) *chosen = h->variant;
   return check_flag(h);
@@ -849,14 +868,15 @@ lbm_status lbm_step_pass(lbm* h, int pass) {
       LBM_CUDA(h, cudaMemsetAsync(h->fix[layout ^ 1], 0, sizeof(unsigned long long) * (size_t)h->N, s));
     } else {
       h->fix_ready = false;
-      LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, nullptr, s));
+      LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, nullptr, h->shape, s));
     }
     h->half = 1;
     return LBM_OK;
   }
   const bool fused = h->variant == 3;
   LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->variant,
-                             fused ? h->fix[layout] : nullptr, fused ? h->fix[layout ^ 1] : nullptr, h->flag, s));
+                             fused ? h->fix[layout] : nullptr, fused ? h->fix[layout ^ 1] : nullptr, h->flag, h->shape,
+                             s));
   if (h->p.bc[5] == LBM_BC_OUTFLOW)
     LBM_CUDA(h, h->ks->outflow(h->pop, h->G, h->P, layout ^ 1, h->top, fused ? h->fix[layout ^ 1] : nullptr, s));
   h->t += 1;

@@ -15,14 +15,15 @@ struct KernelSet {
   size_t real_bytes;      // bytes of the compute type (outflow plane history)
   // pass 1; with fix non-null it writes the fixed-point accumulators of the fused density pass
   // instead of dens (priming the fused pass from a stored state)
+  // shape: block shape of the one-node kernels (0: 32x4x2, 1: 32x2x4, 2: 32x8x1; variants 1 and 3)
   cudaError_t (*density)(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag, void* fix,
-                         cudaStream_t s);
+                         int shape, cudaStream_t s);
   // pass 2.  variant: 1 = one node per thread, 2 = two nodes per thread (FP32 arithmetic, nx even),
   // 3 = one node per thread with the fused density pass (reads cur, accumulates into nxt, which
   // must be zero), 4 = software-pipelined one node per thread (packed storage).  counter: the
   // two-entry step index of k_collide_stream.
   cudaError_t (*collide)(void* pop, const Geom& G, const Phys& P, int odd, const void* dens, long long* counter,
-                         int variant, const void* cur, void* nxt, int* flag, cudaStream_t s);
+                         int variant, const void* cur, void* nxt, int* flag, int shape, cudaStream_t s);
   // convective outflow; with fix non-null it also rewrites the top plane's accumulators
   cudaError_t (*outflow)(void* pop, const Geom& G, const Phys& P, int layout, void* top, void* fix, cudaStream_t s);
   cudaError_t (*init)(void* pop, const Geom& G, const Phys& P, const double* rr, const double* rb, const double* u,

@@ -37,10 +37,21 @@ namespace lbmk {
 enum { BC_PERIODIC = 0, BC_NOSLIP = 1, BC_FREESLIP = 2, BC_INFLOW_WALL = 3, BC_OUTFLOW = 4, BC_HALO = 5 };
 enum { FORCE_NONE = 0, FORCE_BUOYANCY = 1, FORCE_DISPERSED = 2, FORCE_UNIFORM = 3 };
 
-constexpr int BX = 32, BY = 4, BZ = 2;  // pass-2 block: one thread per node
+constexpr int BX = 32, BY = 4, BZ = 2;  // default block: one thread per node
 constexpr int TX = BX + 2, TY = BY + 2, TZ = BZ + 2;
 constexpr int TILE = TX * TY * TZ;
 constexpr int NTHREADS = BX * BY * BZ;
+
+// Block shapes of the one-node density and collide-stream kernels (256 threads each; a warp is
+// always one 32-node x-row): 32 x BY x BZ nodes, and the (rho, phi) halo tile around them.
+template <int BY_, int BZ_>
+struct Blk {
+  static constexpr int BX = 32, BY = BY_, BZ = BZ_;
+  static constexpr int TX = BX + 2, TY = BY + 2, TZ = BZ + 2, TILE = TX * TY * TZ;
+  static constexpr int NT = BX * BY * BZ, NW = NT / 32;
+  static_assert(NT == 256, "256-thread blocks");
+};
+using BlkDefault = Blk<BY, BZ>;
 
 struct Geom {
   int nx, ny, nz;
@@ -702,7 +713,7 @@ __device__ __forceinline__ R red_part(R fstar, const Recol<R>& rc) {
 // all land in the target row (y+dy, z+dz); lane l's target x0+l collects
 // z(l) + p(l-1) + m(l+1), summed with two shuffles; lanes 0 and 31 also write
 // m(0) / p(31) into the edge columns.
-template <int K, bool RECOL, typename R>
+template <int K, bool RECOL, typename R, int BYv = BY, int TXv = TX>
 __device__ __forceinline__ void fused_row(float2* prow, const R f[27], const Recol<R>& rc) {
   const int lane = threadIdx.x;
   const float mt = f[3 * K], zt = f[3 * K + 1], pt = f[3 * K + 2];
@@ -719,10 +730,10 @@ __device__ __forceinline__ void fused_row(float2* prow, const R f[27], const Rec
     st += mt_in;
     sr += mr_in;
   }
-  float2* row = prow + (((threadIdx.y + BY * threadIdx.z) * 9 + K) * TX);
+  float2* row = prow + (((threadIdx.y + BYv * threadIdx.z) * 9 + K) * TXv);
   row[lane + 1] = make_float2(st, sr);
   if (lane == 0) row[0] = make_float2(mt, mr);
-  if (lane == 31) row[TX - 1] = make_float2(pt, pr);
+  if (lane == 31) row[TXv - 1] = make_float2(pt, pr);
 }
 
 // target coordinate along one axis of the slot S(x, t) (c: the component of c_t)
@@ -768,13 +779,13 @@ __device__ __forceinline__ void fused_node(const Geom& G, const FusedIO& io, int
 // grad chi = 3 sum_i w_i chi(x + c_i) c_i (the isotropic stencil of Sec. II).
 // w_i depends only on the speed class |c_i|^2: the neighbours of one class are
 // summed first (signs only), then the class weight multiplies once per component.
-template <int CLS, typename R, typename DT>
+template <int CLS, typename R, typename DT, int TXv = TX, int TYv = TY>
 __device__ __forceinline__ void class_gradients(const DT* tile, int lx, int ly, int lz, R gphi[3], R grho[3]) {
   R sp[3] = {R(0), R(0), R(0)}, sr[3] = {R(0), R(0), R(0)};
 #pragma unroll
   for (int t = 0; t < 27; ++t) {
     if (speed2_of(t) != CLS) continue;
-    const DT v = tile[(lx + cx_of(t)) + TX * ((ly + cy_of(t)) + TY * (lz + cz_of(t)))];
+    const DT v = tile[(lx + cx_of(t)) + TXv * ((ly + cy_of(t)) + TYv * (lz + cz_of(t)))];
     if (cx_of(t) > 0) { sp[0] += (R)v.y; sr[0] += (R)v.x; }
     if (cx_of(t) < 0) { sp[0] -= (R)v.y; sr[0] -= (R)v.x; }
     if (cy_of(t) > 0) { sp[1] += (R)v.y; sr[1] += (R)v.x; }
@@ -793,14 +804,14 @@ __device__ __forceinline__ void class_gradients(const DT* tile, int lx, int ly, 
 // together by one packed FP32x2 add (a fused multiply-add by -1 for a neighbour on the negative
 // side, which rounds exactly like the subtraction): the same operations in the same order as
 // the scalar sums above, half the instructions.  g[k] = (grad rho, grad phi) along axis k.
-template <int CLS>
+template <int CLS, int TXv = TX, int TYv = TY>
 __device__ __forceinline__ void class_gradients2(const float2* tile, int lx, int ly, int lz, float2 g[3]) {
   float2 s[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
   const float2 m1 = make_float2(-1.f, -1.f);
 #pragma unroll
   for (int t = 0; t < 27; ++t) {
     if (speed2_of(t) != CLS) continue;
-    const float2 v = tile[(lx + cx_of(t)) + TX * ((ly + cy_of(t)) + TY * (lz + cz_of(t)))];
+    const float2 v = tile[(lx + cx_of(t)) + TXv * ((ly + cy_of(t)) + TYv * (lz + cz_of(t)))];
     if (cx_of(t) > 0) s[0] = __fadd2_rn(s[0], v);
     if (cx_of(t) < 0) s[0] = __ffma2_rn(v, m1, s[0]);
     if (cy_of(t) > 0) s[1] = __fadd2_rn(s[1], v);
@@ -814,13 +825,13 @@ __device__ __forceinline__ void class_gradients2(const float2* tile, int lx, int
   for (int k = 0; k < 3; ++k) g[k] = __ffma2_rn(w2, s[k], g[k]);
 }
 
-template <typename R, typename DT>
+template <typename R, typename DT, int TXv = TX, int TYv = TY>
 __device__ __forceinline__ void tile_gradients(const DT* tile, int lx, int ly, int lz, R gphi[3], R grho[3]) {
   if constexpr (std::is_same<R, float>::value && std::is_same<DT, float2>::value) {
     float2 g[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    class_gradients2<1>(tile, lx, ly, lz, g);
-    class_gradients2<2>(tile, lx, ly, lz, g);
-    class_gradients2<3>(tile, lx, ly, lz, g);
+    class_gradients2<1, TXv, TYv>(tile, lx, ly, lz, g);
+    class_gradients2<2, TXv, TYv>(tile, lx, ly, lz, g);
+    class_gradients2<3, TXv, TYv>(tile, lx, ly, lz, g);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       grho[k] = g[k].x;
@@ -829,9 +840,9 @@ __device__ __forceinline__ void tile_gradients(const DT* tile, int lx, int ly, i
   } else {
 #pragma unroll
     for (int k = 0; k < 3; ++k) gphi[k] = grho[k] = R(0);
-    class_gradients<1>(tile, lx, ly, lz, gphi, grho);
-    class_gradients<2>(tile, lx, ly, lz, gphi, grho);
-    class_gradients<3>(tile, lx, ly, lz, gphi, grho);
+    class_gradients<1, R, DT, TXv, TYv>(tile, lx, ly, lz, gphi, grho);
+    class_gradients<2, R, DT, TXv, TYv>(tile, lx, ly, lz, gphi, grho);
+    class_gradients<3, R, DT, TXv, TYv>(tile, lx, ly, lz, gphi, grho);
   }
 }
 
@@ -869,7 +880,8 @@ __device__ __forceinline__ void emit(const Store& st, const KConst<R>& K, const 
 
 // FUSED: after each direction (fast rows: each triple of directions), add it to the
 // next step's densities (fused density pass; prow, io as in k_collide_stream)
-template <int T, class Store, typename R, bool FAST, bool RECOL, bool FUSED, int ODDT = -1>
+template <int T, class Store, typename R, bool FAST, bool RECOL, bool FUSED, int ODDT = -1, int BYv = BY,
+          int TXv = TX>
 struct EmitLoop {
   __device__ __forceinline__ static void run(const Store& st, const KConst<R>& K, const Geom& G, const NodeMap& nm,
                                              const AoRow& ar, bool odd, const R* f, const Recol<R>& rc,
@@ -877,16 +889,16 @@ struct EmitLoop {
     emit<T, FAST, RECOL, ODDT>(st, K, G, nm, ar, odd, f, rc);
     if constexpr (FUSED) {
       if constexpr (FAST) {
-        if constexpr (T % 3 == 2) fused_row<T / 3, RECOL>(prow, f, rc);
+        if constexpr (T % 3 == 2) fused_row<T / 3, RECOL, R, BYv, TXv>(prow, f, rc);
       } else {
         fused_node<T>(G, io, x, y, z, f, rc);
       }
     }
-    EmitLoop<T + 1, Store, R, FAST, RECOL, FUSED, ODDT>::run(st, K, G, nm, ar, odd, f, rc, prow, io, x, y, z);
+    EmitLoop<T + 1, Store, R, FAST, RECOL, FUSED, ODDT, BYv, TXv>::run(st, K, G, nm, ar, odd, f, rc, prow, io, x, y, z);
   }
 };
-template <class Store, typename R, bool FAST, bool RECOL, bool FUSED, int ODDT>
-struct EmitLoop<27, Store, R, FAST, RECOL, FUSED, ODDT> {
+template <class Store, typename R, bool FAST, bool RECOL, bool FUSED, int ODDT, int BYv, int TXv>
+struct EmitLoop<27, Store, R, FAST, RECOL, FUSED, ODDT, BYv, TXv> {
   __device__ __forceinline__ static void run(const Store&, const KConst<R>&, const Geom&, const NodeMap&,
                                              const AoRow&, bool, const R*, const Recol<R>&, float2*, const FusedIO&,
                                              int, int, int) {}
@@ -895,16 +907,16 @@ struct EmitLoop<27, Store, R, FAST, RECOL, FUSED, ODDT> {
 // ---------------------------------------------------------------------------
 // pass 1: density / phase field.  FIX: write the fixed-point accumulators of
 // the fused density pass instead (priming the fused pass from a stored state).
-template <class Store, bool FIX>
-__global__ void __launch_bounds__(NTHREADS) k_density(Store st, Geom G,
+template <class Store, bool FIX, class B = BlkDefault>
+__global__ void __launch_bounds__(B::NT) k_density(Store st, Geom G,
                                                       const __grid_constant__ KConst<typename DensOf<Store>::real> K,
                                                       int layout, typename DensOf<Store>::type* __restrict__ dens,
                                                       int* __restrict__ flag,
                                                       unsigned long long* __restrict__ fix) {
   using D = typename DensOf<Store>::real;
-  const int x = blockIdx.x * BX + threadIdx.x;
-  const int y = blockIdx.y * BY + threadIdx.y;
-  const int z = blockIdx.z * BZ + threadIdx.z;
+  const int x = blockIdx.x * B::BX + threadIdx.x;
+  const int y = blockIdx.y * B::BY + threadIdx.y;
+  const int z = blockIdx.z * B::BZ + threadIdx.z;
   if (x >= G.nx || y >= G.ny || z >= G.nz) return;
   D rr = D(0), ft[27];
   if (fast_row(G, y, z)) {
@@ -942,29 +954,29 @@ __global__ void __launch_bounds__(NTHREADS) k_density(Store st, Geom G,
 // captured graph of steps needs no parameter updates.  FUSED: (rho, phi) come
 // from the fixed-point accumulators of the previous step, and the kernel
 // accumulates those of the next step (fused_row, fused_node).
-template <class Store, int MINB, bool FUSED>
-__global__ void __launch_bounds__(NTHREADS, MINB)
+template <class Store, int MINB, bool FUSED, class B = BlkDefault>
+__global__ void __launch_bounds__(B::NT, MINB)
     k_collide_stream(Store st, const __grid_constant__ Geom G,
                      const __grid_constant__ KConst<typename DensOf<Store>::real> K, int odd,
                      const typename DensOf<Store>::type* __restrict__ dens, long long* __restrict__ counter,
                      const FusedIO io) {
   using R = typename DensOf<Store>::real;  // compute type: FP64 for FP64 storage, FP32 otherwise
   using DT = typename DensOf<Store>::type;
-  __shared__ DT tile[TILE];
-  __shared__ float2 prow[FUSED ? NWARPS * 9 * TX : 1];
-  __shared__ int pfast[NWARPS];
+  __shared__ DT tile[B::TILE];
+  __shared__ float2 prow[FUSED ? B::NW * 9 * B::TX : 1];
+  __shared__ int pfast[B::NW];
 
-  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * BZ;
+  const int x0 = blockIdx.x * B::BX, y0 = blockIdx.y * B::BY, z0 = blockIdx.z * B::BZ;
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
   const bool active = x < G.nx && y < G.ny && z < G.nz;
-  const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
+  const int tid = threadIdx.x + B::BX * (threadIdx.y + B::BY * threadIdx.z);
   const long long step = counter[odd];
   if (tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) counter[odd ^ 1] = step + 1;
 
   R rho_r = R(0), ft[27];
   // a warp is one x-row of the block: the fast-row test is warp-uniform (the fused pass sums
   // across the 32 lanes of a fast row, so there the row must also be complete in x)
-  const bool fast = fast_row(G, y, z) && (!FUSED || x0 + BX <= G.nx);
+  const bool fast = fast_row(G, y, z) && (!FUSED || x0 + B::BX <= G.nx);
   if (FUSED && threadIdx.x == 0) pfast[tid >> 5] = active && fast;
   if (active) {
     if (fast) {
@@ -978,7 +990,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
     }
   }
 
-  // halo tile of (rho, phi): warp w fills rows w, w+8, w+16 of the TY*TZ rows of TX
+  // halo tile of (rho, phi): warp w fills rows w, w+8, w+16, ... of the TY*TZ rows of TX
   // values; lanes cover x0-1 .. x0+30 and lanes 0..1 also x0+31, x0+32.
   {
     const int warp = tid >> 5, lane = threadIdx.x;
@@ -987,37 +999,38 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
     const int cxa = xa < G.nx ? xa : G.nx - 1, cxb = xb < G.nx ? xb : G.nx - 1;
     const float rho_r0f = (float)K.rho_r0_d;
 #pragma unroll
-    for (int k = 0; k < (TY * TZ + NTHREADS / 32 - 1) / (NTHREADS / 32); ++k) {
-      const int row = warp + k * (NTHREADS / 32);
-      if (row < TY * TZ) {
-        const int ty = row % TY, tz = row / TY;
+    for (int k = 0; k < (B::TY * B::TZ + B::NT / 32 - 1) / (B::NT / 32); ++k) {
+      const int row = warp + k * (B::NT / 32);
+      if (row < B::TY * B::TZ) {
+        const int ty = row % B::TY, tz = row / B::TY;
         const int gy = wrap_or_clamp(y0 + ty - 1, G.ny, G.bc[2], G.bc[3]);
         const int gz = wrap_or_clamp(z0 + tz - 1, G.nz, G.bc[4], G.bc[5]);
         // out-of-box tail rows of a ragged block read a clamped in-box row
         const int cy = gy < G.ny ? gy : G.ny - 1, cz = gz <= tile_zmax(G) ? gz : tile_zmax(G);
         const int64_t rbase = (int64_t)G.nx * ((int64_t)cy + (int64_t)G.ny * cz);
         if constexpr (FUSED) {
-          tile[row * TX + lane] = fused_cell(io, rbase + cxa);
-          if (lane < TX - 32) tile[row * TX + 32 + lane] = fused_cell(io, rbase + cxb);
+          tile[row * B::TX + lane] = fused_cell(io, rbase + cxa);
+          if (lane < B::TX - 32) tile[row * B::TX + 32 + lane] = fused_cell(io, rbase + cxb);
         } else {
-          tile[row * TX + lane] = dens[rbase + cxa];
-          if (lane < TX - 32) tile[row * TX + 32 + lane] = dens[rbase + cxb];
+          tile[row * B::TX + lane] = dens[rbase + cxa];
+          if (lane < B::TX - 32) tile[row * B::TX + 32 + lane] = dens[rbase + cxb];
         }
       }
     }
     if constexpr (FUSED) {
-      if (G.inflow && z0 == 0) {
-        // the Dirichlet inlet nodes carry rho_r0 and phi = 1, as in pass 1; tile planes 0 (z = -1,
-        // mirrored onto z = 0) and 1 (z = 0).  Block-uniform branch.
+      if (G.inflow && z0 <= 1) {
+        // the Dirichlet inlet nodes carry rho_r0 and phi = 1, as in pass 1: in the tile planes that
+        // read the z = 0 plane (for z0 = 0: plane 0, the mirror ghost z = -1, and plane 1; for
+        // z0 = 1, which 32 x BY x 1 blocks reach: plane 0).  Block-uniform branch.
         __syncthreads();
-        for (int c = tid; c < TX * TY; c += NTHREADS) {
-          int gx = wrap_or_clamp(x0 + c % TX - 1, G.nx, G.bc[0], G.bc[1]);
-          int gy = wrap_or_clamp(y0 + c / TX - 1, G.ny, G.bc[2], G.bc[3]);
+        for (int c = tid; c < B::TX * B::TY; c += B::NT) {
+          int gx = wrap_or_clamp(x0 + c % B::TX - 1, G.nx, G.bc[0], G.bc[1]);
+          int gy = wrap_or_clamp(y0 + c / B::TX - 1, G.ny, G.bc[2], G.bc[3]);
           gx = gx < G.nx ? gx : G.nx - 1;
           gy = gy < G.ny ? gy : G.ny - 1;
           if (is_inlet(G, gx, gy, 0)) {
-            tile[c] = make_float2(rho_r0f, 1.0f);
-            tile[c + TX * TY] = make_float2(rho_r0f, 1.0f);
+            tile[c] = make_float2(rho_r0f, 1.0f);  // plane 0: z = -1 (z0 = 0) or z = 0 (z0 = 1)
+            if (z0 == 0) tile[c + B::TX * B::TY] = make_float2(rho_r0f, 1.0f);
           }
         }
       }
@@ -1028,7 +1041,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
 
   if (active) {
     R gphi[3], grho[3];
-    tile_gradients<R>(tile, threadIdx.x + 1, threadIdx.y + 1, threadIdx.z + 1, gphi, grho);
+    tile_gradients<R, DT, B::TX, B::TY>(tile, threadIdx.x + 1, threadIdx.y + 1, threadIdx.z + 1, gphi, grho);
 
     R f[27];
     Recol<R> rc;
@@ -1055,20 +1068,20 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
       // the parity as a template argument: no per-direction branch on it in the stores (the
       // fused density pass keeps it a runtime value: the extra code raised its spills)
       if constexpr (FUSED) {
-        if (recol) EmitLoop<0, Store, R, true, true, FUSED>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
-        else EmitLoop<0, Store, R, true, false, FUSED>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
+        if (recol) EmitLoop<0, Store, R, true, true, FUSED, -1, B::BY, B::TX>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
+        else EmitLoop<0, Store, R, true, false, FUSED, -1, B::BY, B::TX>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
       } else if (recol) {
-        if (odd) EmitLoop<0, Store, R, true, true, FUSED, 1>::run(st, K, G, nm, ar, true, f, rc, prow, io, x, y, z);
-        else EmitLoop<0, Store, R, true, true, FUSED, 0>::run(st, K, G, nm, ar, false, f, rc, prow, io, x, y, z);
+        if (odd) EmitLoop<0, Store, R, true, true, FUSED, 1, B::BY, B::TX>::run(st, K, G, nm, ar, true, f, rc, prow, io, x, y, z);
+        else EmitLoop<0, Store, R, true, true, FUSED, 0, B::BY, B::TX>::run(st, K, G, nm, ar, false, f, rc, prow, io, x, y, z);
       } else {
-        if (odd) EmitLoop<0, Store, R, true, false, FUSED, 1>::run(st, K, G, nm, ar, true, f, rc, prow, io, x, y, z);
-        else EmitLoop<0, Store, R, true, false, FUSED, 0>::run(st, K, G, nm, ar, false, f, rc, prow, io, x, y, z);
+        if (odd) EmitLoop<0, Store, R, true, false, FUSED, 1, B::BY, B::TX>::run(st, K, G, nm, ar, true, f, rc, prow, io, x, y, z);
+        else EmitLoop<0, Store, R, true, false, FUSED, 0, B::BY, B::TX>::run(st, K, G, nm, ar, false, f, rc, prow, io, x, y, z);
       }
     } else {
       if (odd) nm.init(G, x, y, z);
       else nm.base = snode(G, x, y, z);  // the even step only uses the base
-      if (recol) EmitLoop<0, Store, R, false, true, FUSED>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
-      else EmitLoop<0, Store, R, false, false, FUSED>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
+      if (recol) EmitLoop<0, Store, R, false, true, FUSED, -1, B::BY, B::TX>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
+      else EmitLoop<0, Store, R, false, false, FUSED, -1, B::BY, B::TX>::run(st, K, G, nm, ar, odd != 0, f, rc, prow, io, x, y, z);
     }
   }
 
@@ -1081,26 +1094,26 @@ __global__ void __launch_bounds__(NTHREADS, MINB)
     int gxa = x0 - 1 + lane, gxb = x0 + 31 + lane;  // lanes 0..1 also take columns 32, 33
     if (gxa < 0) gxa = G.bc[0] == BC_PERIODIC ? G.nx - 1 : 0;
     if (gxb >= G.nx) gxb = G.bc[1] == BC_PERIODIC ? gxb - G.nx : G.nx - 1;
-    const bool ina = gxa < G.nx, inb = lane < TX - 32 && gxb >= 0 && gxb < G.nx;
+    const bool ina = gxa < G.nx, inb = lane < B::TX - 32 && gxb >= 0 && gxb < G.nx;
 #pragma unroll
-    for (int k = 0; k < (TY * TZ + NWARPS - 1) / NWARPS; ++k) {
-      const int row = warp + k * NWARPS;
-      if (row < TY * TZ) {
-        const int ty = row % TY, tz = row / TY;
+    for (int k = 0; k < (B::TY * B::TZ + B::NW - 1) / B::NW; ++k) {
+      const int row = warp + k * B::NW;
+      if (row < B::TY * B::TZ) {
+        const int ty = row % B::TY, tz = row / B::TY;
         const int gy = y0 - 1 + ty, gz = z0 - 1 + tz;
         if (gy >= 0 && gy < G.ny && gz >= 0 && gz < G.nz) {
           float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int wz = 0; wz < BZ; ++wz) {
+          for (int wz = 0; wz < B::BZ; ++wz) {
 #pragma unroll
-            for (int wy = 0; wy < BY; ++wy) {
+            for (int wy = 0; wy < B::BY; ++wy) {
               const int ky = ty - wy, kz = tz - wz;
-              if (ky >= 0 && ky <= 2 && kz >= 0 && kz <= 2 && pfast[wy + BY * wz]) {
-                const float2* src = prow + ((wy + BY * wz) * 9 + ky + 3 * kz) * TX;
+              if (ky >= 0 && ky <= 2 && kz >= 0 && kz <= 2 && pfast[wy + B::BY * wz]) {
+                const float2* src = prow + ((wy + B::BY * wz) * 9 + ky + 3 * kz) * B::TX;
                 const float2 u = src[lane];
                 a.x += u.x;
                 a.y += u.y;
-                if (lane < TX - 32) {
+                if (lane < B::TX - 32) {
                   const float2 v = src[32 + lane];
                   b.x += v.x;
                   b.y += v.y;

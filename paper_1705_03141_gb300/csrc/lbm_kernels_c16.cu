@@ -13,14 +13,14 @@ struct LaunchCompact {
                  G.Ns};
   }
   static KConst<float> kc(const Phys& P) { return make_kconst<float>(P); }
-  static cudaError_t density(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag, void*,
+  static cudaError_t density(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag, void*, int,
                              cudaStream_t s) {
     k_density_c<B><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(make(pop, G), G, kc(P), layout, static_cast<float2*>(dens),
                                                           flag);
     return cudaGetLastError();
   }
   static cudaError_t collide(void* pop, const Geom& G, const Phys& P, int odd, const void* dens, long long* counter,
-                             int, const void*, void*, int*, cudaStream_t s) {
+                             int, const void*, void*, int*, int, cudaStream_t s) {
     k_collide_stream_c<B><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(make(pop, G), G, kc(P), odd,
                                                                  static_cast<const float2*>(dens), counter);
     return cudaGetLastError();

@@ -5,8 +5,10 @@
 
 namespace lbmk {
 
+template <class B = BlkDefault>
 inline dim3 grid3(const Geom& G) {
-  return dim3((unsigned)((G.nx + BX - 1) / BX), (unsigned)((G.ny + BY - 1) / BY), (unsigned)((G.nz + BZ - 1) / BZ));
+  return dim3((unsigned)((G.nx + B::BX - 1) / B::BX), (unsigned)((G.ny + B::BY - 1) / B::BY),
+              (unsigned)((G.nz + B::BZ - 1) / B::BZ));
 }
 inline unsigned blocks1(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -44,21 +46,44 @@ struct Launch {
   static constexpr bool fused = !std::is_same<R, double>::value;
   static constexpr bool pipelined = Store::PLANES == 27;  // packed storage
 
-  static cudaError_t density(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag, void* fix,
-                             cudaStream_t s) {
+  template <class B>
+  static cudaError_t density_b(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag, void* fix,
+                               cudaStream_t s) {
     if constexpr (fused) {
       if (fix) {
-        k_density<Store, true><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(
+        k_density<Store, true, B><<<grid3<B>(G), dim3(B::BX, B::BY, B::BZ), 0, s>>>(
             Tr::make(pop, G), G, kc(P), layout, static_cast<DT*>(dens), flag, static_cast<unsigned long long*>(fix));
         return cudaGetLastError();
       }
     }
-    k_density<Store, false><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(Tr::make(pop, G), G, kc(P), layout,
-                                                                  static_cast<DT*>(dens), flag, nullptr);
+    k_density<Store, false, B><<<grid3<B>(G), dim3(B::BX, B::BY, B::BZ), 0, s>>>(
+        Tr::make(pop, G), G, kc(P), layout, static_cast<DT*>(dens), flag, nullptr);
+    return cudaGetLastError();
+  }
+  static cudaError_t density(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag, void* fix,
+                             int shape, cudaStream_t s) {
+    if constexpr (!std::is_same<R, double>::value) {  // FP64 keeps the default shape
+      if (shape == 1) return density_b<Blk<2, 4>>(pop, G, P, layout, dens, flag, fix, s);
+      if (shape == 2) return density_b<Blk<8, 1>>(pop, G, P, layout, dens, flag, fix, s);
+    }
+    return density_b<BlkDefault>(pop, G, P, layout, dens, flag, fix, s);
+  }
+  template <class B>
+  static cudaError_t collide_b(void* pop, const Geom& G, const Phys& P, int odd, const void* dens, long long* counter,
+                               bool fused_pass, const FusedIO& io, cudaStream_t s) {
+    if constexpr (fused) {
+      if (fused_pass) {
+        k_collide_stream<Store, Tr::minb, true, B><<<grid3<B>(G), dim3(B::BX, B::BY, B::BZ), 0, s>>>(
+            Tr::make(pop, G), G, kc(P), odd, static_cast<const DT*>(dens), counter, io);
+        return cudaGetLastError();
+      }
+    }
+    k_collide_stream<Store, Tr::minb, false, B><<<grid3<B>(G), dim3(B::BX, B::BY, B::BZ), 0, s>>>(
+        Tr::make(pop, G), G, kc(P), odd, static_cast<const DT*>(dens), counter, io);
     return cudaGetLastError();
   }
   static cudaError_t collide(void* pop, const Geom& G, const Phys& P, int odd, const void* dens, long long* counter,
-                             int variant, const void* cur, void* nxt, int* flag, cudaStream_t s) {
+                             int variant, const void* cur, void* nxt, int* flag, int shape, cudaStream_t s) {
     if constexpr (Tr::paired) {
       if (variant == 2) {
         k_collide_stream2<Store, Tr::minb2><<<grid3(G), dim3(PX, PY, PZ), 0, s>>>(
@@ -87,16 +112,12 @@ struct Launch {
       }
     }
     FusedIO io{static_cast<const unsigned long long*>(cur), static_cast<unsigned long long*>(nxt), flag};
-    if constexpr (fused) {
-      if (variant == 3) {
-        k_collide_stream<Store, Tr::minb, true><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(
-            Tr::make(pop, G), G, kc(P), odd, static_cast<const DT*>(dens), counter, io);
-        return cudaGetLastError();
-      }
+    const bool fp = variant == 3;
+    if constexpr (!std::is_same<R, double>::value) {
+      if (shape == 1) return collide_b<Blk<2, 4>>(pop, G, P, odd, dens, counter, fp, io, s);
+      if (shape == 2) return collide_b<Blk<8, 1>>(pop, G, P, odd, dens, counter, fp, io, s);
     }
-    k_collide_stream<Store, Tr::minb, false><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(
-        Tr::make(pop, G), G, kc(P), odd, static_cast<const DT*>(dens), counter, io);
-    return cudaGetLastError();
+    return collide_b<BlkDefault>(pop, G, P, odd, dens, counter, fp, io, s);
   }
   static cudaError_t outflow(void* pop, const Geom& G, const Phys& P, int layout, void* top, void* fix,
                              cudaStream_t s) {

@@ -28,7 +28,7 @@ SYMBOLS = ["lbm_workspace_size", "lbm_create", "lbm_init_fields", "lbm_set_inflo
            "lbm_diag", "lbm_get_populations", "lbm_set_populations", "lbm_profile_step", "lbm_set_stream", "lbm_synchronize", "lbm_time",
            "lbm_kernels_per_step", "lbm_last_error", "lbm_status_string", "lbm_moment_matrix", "lbm_selfcheck",
            "lbm_diag_fields_static", "lbm_autotune", "lbm_batch_create", "lbm_batch_step", "lbm_batch_synchronize",
-           "lbm_batch_free", "lbm_measure_fp32_peak", "lbm_kernel_variant", "lbm_halo_bytes", "lbm_halo_pack",
+           "lbm_batch_free", "lbm_measure_fp32_peak", "lbm_kernel_variant", "lbm_kernel_block", "lbm_halo_bytes", "lbm_halo_pack",
            "lbm_halo_unpack", "lbm_step_pass", "lbm_free"]
 
 
@@ -53,6 +53,7 @@ class Params(ctypes.Structure):
         ("workspace", ctypes.c_void_p),
         ("workspace_bytes", ctypes.c_size_t),
         ("variant", ctypes.c_int),
+        ("block", ctypes.c_int),
     ]
 
 
@@ -84,6 +85,7 @@ def library():
         lib.lbm_time.restype = ctypes.c_longlong
         lib.lbm_kernels_per_step.argtypes = [h]
         lib.lbm_kernel_variant.argtypes = [h]
+        lib.lbm_kernel_block.argtypes = [h]
         lib.lbm_last_error.argtypes = [h]
         lib.lbm_last_error.restype = ctypes.c_char_p
         lib.lbm_status_string.argtypes = [i]
@@ -111,7 +113,8 @@ def library():
     return _lib
 
 
-def _params_struct(p: dict, storage: int, stream=None, workspace=None, workspace_bytes=0, variant=0) -> Params:
+def _params_struct(p: dict, storage: int, stream=None, workspace=None, workspace_bytes=0, variant=0,
+                   block=0) -> Params:
     s = Params()
     s.rho_r0, s.rho_b0 = float(p["rho_r0"]), float(p["rho_b0"])
     s.nu_r, s.nu_b = float(p["nu_r"]), float(p["nu_b"])
@@ -130,6 +133,7 @@ def _params_struct(p: dict, storage: int, stream=None, workspace=None, workspace
     s.workspace = workspace
     s.workspace_bytes = int(workspace_bytes)
     s.variant = int(variant)
+    s.block = int(block)
     return s
 
 
@@ -219,7 +223,7 @@ class Lattice:
     current CUDA stream at creation time (``set_stream`` changes it).
     """
 
-    def __init__(self, shape, params: dict, storage="f32", device=None, stream=None, variant=0):
+    def __init__(self, shape, params: dict, storage="f32", device=None, stream=None, variant=0, block=0):
         import torch
 
         self.nx, self.ny, self.nz = (int(v) for v in shape)
@@ -230,12 +234,13 @@ class Lattice:
         with torch.cuda.device(self.device):
             st = torch.cuda.current_stream(self.device) if stream is None else stream
             self.stream = st
-            probe = _params_struct(self.params, self.storage, variant=variant)
+            probe = _params_struct(self.params, self.storage, variant=variant, block=block)
             nbytes = ctypes.c_size_t()
             _check(lib.lbm_workspace_size(self.nx, self.ny, self.nz, ctypes.byref(probe), ctypes.byref(nbytes)), None)
             self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
             ps = _params_struct(self.params, self.storage, stream=st.cuda_stream,
-                                workspace=self.workspace.data_ptr(), workspace_bytes=nbytes.value, variant=variant)
+                                workspace=self.workspace.data_ptr(), workspace_bytes=nbytes.value, variant=variant,
+                                block=block)
             h = ctypes.c_void_p()
             _check(lib.lbm_create(self.nx, self.ny, self.nz, ctypes.byref(ps), ctypes.byref(h)), None)
         self._h = h
@@ -276,8 +281,14 @@ class Lattice:
 
     @property
     def variant(self):
-        """Collide-stream kernel in use: 1 one node per thread, 2 two nodes, 3 fused density pass."""
+        """Collide-stream kernel in use: 1 one node per thread, 2 two nodes, 3 fused density pass,
+        4 software-pipelined."""
         return library().lbm_kernel_variant(self._h)
+
+    @property
+    def block(self):
+        """Block shape of the one-node kernels: 1 = 32x4x2, 2 = 32x2x4, 3 = 32x8x1."""
+        return library().lbm_kernel_block(self._h)
 
     def set_stream(self, stream):
         self.stream = stream
@@ -326,7 +337,8 @@ class Lattice:
         _check(library().lbm_synchronize(self._h), self._h)
 
     def autotune(self, steps=8):
-        """Time both collide-stream kernels on `steps` real steps each; keep the faster (returns 1 or 2)."""
+        """Time every collide-stream variant (and, for variants 1 and 3, every block shape) on `steps`
+        real steps each; keep the fastest.  Returns the variant (see `block` for the shape)."""
         c = ctypes.c_int()
         _check(library().lbm_autotune(self._h, int(steps), ctypes.byref(c)), self._h)
         return c.value
