@@ -68,7 +68,7 @@ def peaks():
 
 
 KERNEL_SOURCES = ("lbm_f2.cuh", "lbm_kernels.cuh", "lbm_kernels_f16.cu", "lbm_kernels_f32.cu", "lbm_kernels_f64.cu",
-                  "lbm_lattice.cuh", "lbm_launch.cuh")
+                  "lbm_lattice.cuh", "lbm_launch.cuh", "lbm_compact.cuh", "lbm_kernels_c16.cu")
 
 
 def kernel_hash():
@@ -82,6 +82,9 @@ def kernel_hash():
 
 def profile_name(storage, variant):
     return f"collide_stream{ {3: '_fused', 4: '_pipelined'}.get(variant, '') }_jet_{storage}.md"
+
+
+KERNEL_REGEX = {"c16": "k_collide_stream_c", "cbf16": "k_collide_stream_c"}
 
 
 def collide_bytes(storage, variant):
