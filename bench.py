@@ -52,7 +52,7 @@ UNIT = "MLUPS"
 POP_BYTES = {"f64": 8 * 54, "f32": 4 * 54, "f16": 4 * 27, "bf16": 4 * 27, "c16": 56, "cbf16": 56}
 DENS_BYTES = {"f64": 16, "f32": 8, "f16": 8, "bf16": 8, "c16": 8, "cbf16": 8}
 RECORD_BYTES = {"c16": 16, "cbf16": 16}
-BLOCKS = {1: "32x4x2", 2: "32x2x4", 3: "32x8x1"}
+BLOCKS = {1: "32x4x2", 2: "32x2x4", 3: "32x8x1", 4: "32x4x2 tiles, TMA-pipelined pass 1"}
 
 
 def workload(seed=1234):
@@ -68,7 +68,7 @@ def peaks():
 
 
 KERNEL_SOURCES = ("lbm_f2.cuh", "lbm_kernels.cuh", "lbm_kernels_f16.cu", "lbm_kernels_f32.cu", "lbm_kernels_f64.cu",
-                  "lbm_lattice.cuh", "lbm_launch.cuh", "lbm_compact.cuh", "lbm_kernels_c16.cu")
+                  "lbm_lattice.cuh", "lbm_launch.cuh", "lbm_compact.cuh", "lbm_kernels_c16.cu", "lbm_tma.cuh")
 
 
 def kernel_hash():
@@ -385,7 +385,7 @@ def main():
     ap.add_argument("--variant", type=int, default=0, help="collide-stream kernel: 0 library choice, 1 one node "
                     "per thread, 2 two nodes per thread, 3 fused density pass, 4 software-pipelined (packed)")
     ap.add_argument("--block", type=int, default=0, help="block shape of the one-node kernels: 0 library choice, "
-                    "1 32x4x2, 2 32x2x4, 3 32x8x1")
+                    "1 32x4x2, 2 32x2x4, 3 32x8x1, 4 pipelined density pass (compact storage)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

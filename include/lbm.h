@@ -52,7 +52,7 @@ typedef enum {
   LBM_ENOMEM = -2,    /* device or host allocation failed, or workspace too small */
   LBM_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
   LBM_EUNSTABLE = -4, /* the watchdog saw a non-finite or non-positive density */
-  LBM_ETIMEOUT = -5,  /* reserved for bounded device-side waits */
+  LBM_ETIMEOUT = -5,  /* a bounded device-side wait ran out (the TMA-pipelined pass 1 of compact storage) */
   LBM_ESTATE = -6     /* call not valid in the handle's current state */
 } lbm_status;
 
@@ -168,8 +168,17 @@ typedef struct {
                             32-node x-row in each).  Variant 1 computes the same
                             update bitwise in every shape; variant 3 differs by FP32
                             rounding (how the next step's densities are grouped
-                            before their exact fixed-point sum).  FP64 and compact
-                            storage always run 32x4x2. */
+                            before their exact fixed-point sum).  FP64 storage
+                            always runs 32x4x2.  Compact storage (F16C/BF16C) runs
+                            32x4x2 tiles with one of two density passes: 1 = one
+                            block per tile, 4 = persistent blocks of 8 consumer
+                            warps and one producer warp that streams each tile's
+                            totals and colour records into a 3-stage shared-memory
+                            ring with TMA copies (needs x faces that are neither
+                            periodic nor no-slip; the library's choice there, and
+                            bitwise the same densities as 1).  Any other storage
+                            with block 4, or compact storage with 2 or 3, gives
+                            LBM_EINVAL. */
 } lbm_params;
 
 typedef struct lbm lbm; /* opaque handle; owns all device state it allocated */
@@ -255,8 +264,9 @@ LBM_EXPORT int lbm_kernels_per_step(const lbm* h);
 LBM_EXPORT int lbm_kernel_variant(const lbm* h);
 
 /* The block shape the handle's one-node kernels run (1 = 32x4x2, 2 = 32x2x4,
- * 3 = 32x8x1: lbm_params.block, the library's choice, or the one lbm_autotune
- * chose); -1 for NULL. */
+ * 3 = 32x8x1, 4 = 32x4x2 tiles with the TMA-pipelined compact density pass:
+ * lbm_params.block, the library's choice, or the one lbm_autotune chose); -1
+ * for NULL. */
 LBM_EXPORT int lbm_kernel_block(const lbm* h);
 
 /* Last error message of this handle ("" if none); valid until the next call. */
@@ -279,7 +289,8 @@ LBM_EXPORT lbm_status lbm_selfcheck(const char** msg);
  * `steps` steps (>= 1) with each available variant (1; 2 where the storage and
  * nx allow; 3 for F32/F16/BF16 storage; 4 for F16/BF16 storage), variants 1
  * and 3 in each of the three block shapes of lbm_params.block (FP32-arithmetic
- * storages other than compact), timed with CUDA events on the handle's stream,
+ * storages other than compact; compact storage: block 1 and, where its x faces
+ * allow, block 4), timed with CUDA events on the handle's stream,
  * keep the fastest (variant, shape) for later steps and report the variant in
  * *chosen (1 to 4; may be NULL; lbm_kernel_block gives the shape).  The tuning
  * steps are ordinary time steps of the same update, so the time advances by

@@ -13,6 +13,7 @@
 #include "../../include/lbm.h"
 #include "lbm_dispatch.h"
 #include "lbm_kernels.cuh"
+#include "lbm_tma.cuh"
 
 using lbmk::Geom;
 using lbmk::KernelSet;
@@ -54,6 +55,7 @@ struct lbm {
   cudaGraphExec_t graph[2];  // kGraphSteps steps starting at an even / odd step
   long long t;
   bool unstable;
+  bool timed_out;  // a bounded device-side wait ran out (flag bit kFlagTimeout)
   bool halo;     // a z face is LBM_BC_HALO: the handle is one slab of a decomposed domain
   bool recs_valid;  // compact storage: the colour records describe the current state
   bool dens_ready;  // compact storage: dens holds (rho, phi) of the current state
@@ -93,10 +95,22 @@ const KernelSet* kernels_for(int storage) {
   }
 }
 
+// where the pipelined compact pass 1 applies: x faces that reflect (free-slip), no row whose last
+// 32-node block holds a single node (that lane would be both block edges), and at least three
+// 32x4x2 tiles along y and z (the tiles next to the faces go to the one-block kernel)
+bool pipelined_ok(int nx, int ny, int nz, const lbm_params* p) {
+  return p->bc[0] != LBM_BC_PERIODIC && p->bc[1] != LBM_BC_PERIODIC && p->bc[0] != LBM_BC_NOSLIP &&
+         p->bc[1] != LBM_BC_NOSLIP && nx % 32 != 1 && ny > 2 * lbmk::BY && nz > 2 * lbmk::BZ;
+}
+
 const char* validate(int nx, int ny, int nz, const lbm_params* p) {
   if (!p) return "params is NULL";
   if (nx < 3 || ny < 3 || nz < 3) return "each box dimension must be >= 3";
   if ((double)nx * ny * nz >= 2147483647.0 / 2) return "box too large (nx*ny*nz must stay below 2^30)";
+  // the kernels address a node's slots by 32-bit offsets from its own: one z plane of storage
+  // (up to 54 values per node) must hold fewer than 2^31 elements
+  if ((double)align_up((size_t)nx, 32) * ny * 54.0 >= 2147483647.0 - 65536.0)
+    return "xy plane too large (nx rounded up to 32, times ny, times 54 must stay below 2^31)";
   if (!(p->rho_r0 > 0) || !(p->rho_b0 > 0)) return "rho_r0 and rho_b0 must be > 0";
   const double ab = 8.0 / 27.0, ar = 1.0 - (1.0 - ab) / (p->rho_r0 / p->rho_b0);
   if (!(ar >= 0.0 && ar < 1.0)) return "density ratio rho_r0/rho_b0 must be >= 19/27 (alpha_r in [0,1))";
@@ -124,11 +138,18 @@ const char* validate(int nx, int ny, int nz, const lbm_params* p) {
     if (p->bc[f] == LBM_BC_OUTFLOW && f != 5) return "OUTFLOW is only allowed on the +z face";
   }
   if (p->storage < 0 || p->storage > 5) return "unknown storage";
-  if (p->block < 0 || p->block > 3) return "unknown block shape (0: library's choice, 1: 32x4x2, 2: 32x2x4, 3: 32x8x1)";
-  if (p->storage == LBM_STORE_F16C || p->storage == LBM_STORE_BF16C) {
+  if (p->block < 0 || p->block > 4)
+    return "unknown block shape (0: library's choice, 1: 32x4x2, 2: 32x2x4, 3: 32x8x1, 4: pipelined compact pass 1)";
+  const bool compact = p->storage == LBM_STORE_F16C || p->storage == LBM_STORE_BF16C;
+  if (compact) {
     if (p->variant > 1) return "compact storage runs the one-node collide-stream kernel (variant 0 or 1)";
     if (p->bc[4] == LBM_BC_HALO || p->bc[5] == LBM_BC_HALO) return "compact storage has no z-slab halo exchange";
+    if (p->block == 2 || p->block == 3)
+      return "compact storage runs 32x4x2 tiles: block 0, 1 or 4 (pipelined pass 1)";
   }
+  if (p->block == 4 && !(compact && pipelined_ok(nx, ny, nz, p)))
+    return "block 4 (TMA-pipelined pass 1) needs compact storage, x faces that are neither periodic nor no-slip, "
+           "nx % 32 != 1, ny > 8 and nz > 4";
   if (p->variant < 0 || p->variant > 4) return "unknown kernel variant";
   if (p->variant == 4 && p->storage != LBM_STORE_F16 && p->storage != LBM_STORE_BF16)
     return "the software-pipelined kernel needs packed (F16/BF16) storage";
@@ -272,13 +293,20 @@ lbm_status compact_dens(lbm* h) {
   return LBM_OK;
 }
 
+// the errors a kernel reported through the flag stay with the handle until the next upload
+lbm_status sticky_status(lbm* h) {
+  if (h->timed_out) return fail(h, LBM_ETIMEOUT, "a bounded device-side wait of a pipelined kernel ran out");
+  if (h->unstable) return fail(h, LBM_EUNSTABLE, "watchdog: non-finite or non-positive density seen");
+  return LBM_OK;
+}
+
 lbm_status check_flag(lbm* h) {
   int flag = 0;
   LBM_CUDA(h, cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   LBM_CUDA(h, cudaStreamSynchronize(h->stream));
-  if (flag) h->unstable = true;
-  if (h->unstable) return fail(h, LBM_EUNSTABLE, "watchdog: non-finite or non-positive density seen");
-  return LBM_OK;
+  if (flag & lbmk::kFlagTimeout) h->timed_out = true;
+  if (flag & ~lbmk::kFlagTimeout) h->unstable = true;
+  return sticky_status(h);
 }
 
 }  // namespace
@@ -336,6 +364,8 @@ lbm_status lbm_create(int nx, int ny, int nz, const lbm_params* p, lbm** out) {
   // block shape: as measured on GB300 (128x128x512 jet), the fused FP32 kernel runs fastest in
   // 32x2x4 blocks (0.784 against 0.814 ms for 32x4x2); every other kernel in 32x4x2
   h->shape = p->block != 0 ? p->block - 1 : (h->variant == 3 && p->storage == LBM_STORE_F32 ? 1 : 0);
+  // compact storage: the TMA-pipelined pass 1 wherever it applies (0.11 against 0.36 ms on the jet)
+  if (h->ks->compact && p->block == 0 && pipelined_ok(nx, ny, nz, p)) h->shape = 3;
 
   Geom& G = h->G;
   G.nx = nx;
@@ -470,6 +500,7 @@ lbm_status lbm_init_fields(lbm* h, const double* rhoR, const double* rhoB, const
     LBM_CUDA(h, h->ks->top_from_state(h->pop, h->G, h->P, 0, h->top, h->stream));
   LBM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->unstable = false;
+  h->timed_out = false;
   return LBM_OK;
 }
 
@@ -491,7 +522,7 @@ lbm_status lbm_set_inflow(lbm* h, double xc, double yc, double D, double u_j0, d
 
 lbm_status lbm_step(lbm* h, int n) {
   if (!h || n < 0) return h ? fail(h, LBM_EINVAL, "n must be >= 0") : LBM_EINVAL;
-  if (h->unstable) return fail(h, LBM_EUNSTABLE, "watchdog: non-finite or non-positive density seen");
+  if (h->unstable || h->timed_out) return sticky_status(h);
   if (h->halo) return fail(h, LBM_ESTATE, "slab handles (HALO faces) step with lbm_step_pass and halo exchanges");
   if (h->half) return fail(h, LBM_ESTATE, "a step begun with lbm_step_pass(h, 1) must end with lbm_step_pass(h, 2)");
   static const bool no_graphs = getenv("LBM_NO_GRAPHS") != nullptr;
@@ -638,13 +669,14 @@ lbm_status lbm_set_populations(lbm* h, const double* f, long long t) {
     LBM_CUDA(h, h->ks->top_from_state(h->pop, h->G, h->P, layout, h->top, h->stream));
   LBM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->unstable = false;
+  h->timed_out = false;
   return LBM_OK;
 }
 
 lbm_status lbm_profile_step(lbm* h, int n, double* ms_out) {
   if (!h) return LBM_EINVAL;
   if (n < 1 || !ms_out) return fail(h, LBM_EINVAL, "need n >= 1 and an output array of 3 doubles");
-  if (h->unstable) return fail(h, LBM_EUNSTABLE, "watchdog: non-finite or non-positive density seen");
+  if (h->unstable || h->timed_out) return sticky_status(h);
   if (h->halo || h->half) return fail(h, LBM_ESTATE, "not available on slab handles or between step passes");
   if (h->ks->compact && !h->recs_valid)
     return fail(h, LBM_ESTATE, "compact storage: take one lbm_step after an upload before profiling");
@@ -792,13 +824,13 @@ lbm_status lbm_selfcheck(const char** msg) {
 lbm_status lbm_autotune(lbm* h, int steps, int* chosen) {
   if (!h) return LBM_EINVAL;
   if (steps < 1) return fail(h, LBM_EINVAL, "steps must be >= 1");
-  if (h->unstable) return fail(h, LBM_EUNSTABLE, "watchdog: non-finite or non-positive density seen");
+  if (h->unstable || h->timed_out) return sticky_status(h);
   if (h->halo || h->half) return fail(h, LBM_ESTATE, "not available on slab handles or between step passes");
   if (h->ks->compact && !h->recs_valid)
     return fail(h, LBM_ESTATE, "compact storage: take one lbm_step after an upload before autotuning");
   if (h->ks->compact) h->dens_ready = false;
   // candidates: (variant, block shape); the shapes apply to the one-node kernels (variants 1, 3)
-  // of the FP32-arithmetic storages
+  // of the FP32-arithmetic storages; compact storage: one-block or pipelined pass 1
   int cand[12][2], nc = 0;
   const bool shapes = !h->ks->compact && h->p.storage != LBM_STORE_F64;
   for (int v = 1; v <= 4; ++v) {
@@ -810,6 +842,11 @@ lbm_status lbm_autotune(lbm* h, int steps, int* chosen) {
       cand[nc][1] = b;
       ++nc;
     }
+  }
+  if (h->ks->compact && pipelined_ok(h->nx, h->ny, h->nz, &h->p)) {
+    cand[nc][0] = 1;
+    cand[nc][1] = 3;
+    ++nc;
   }
   float ms[12] = {0.f};
   cudaEvent_t e0, e1;
@@ -852,7 +889,7 @@ lbm_status lbm_autotune(lbm* h, int steps, int* chosen) {
 lbm_status lbm_step_pass(lbm* h, int pass) {
   if (!h) return LBM_EINVAL;
   if (pass != 1 && pass != 2) return fail(h, LBM_EINVAL, "pass must be 1 or 2");
-  if (h->unstable) return fail(h, LBM_EUNSTABLE, "watchdog: non-finite or non-positive density seen");
+  if (h->unstable || h->timed_out) return sticky_status(h);
   if (pass != h->half + 1) return fail(h, LBM_ESTATE, "passes must alternate 1, 2, 1, 2, ...");
   const long long t = h->t;
   const int layout = (int)(t & 1);
@@ -1068,6 +1105,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int n) {
   const long long t0 = b->h[0]->t;
   for (lbm* h : b->h) {
     if (((h->t - t0) & 1) != 0 || h->half || (h->ks->compact && !h->recs_valid)) return LBM_ESTATE;
+    if (h->timed_out) return LBM_ETIMEOUT;
     if (h->unstable) return LBM_EUNSTABLE;
   }
   // the batch stream first waits for whatever each handle's own stream has queued ...

@@ -223,6 +223,7 @@ struct NodeMap {
 // nx in the last block of a row are idle; their padding slots are never used.)
 struct AoRow {
   int64_t e[3];
+  int dxm, dxp;  // e[0] - e[1] and e[2] - e[1]
   template <int PLANES>
   __device__ __forceinline__ void init(const Geom& g, int x, int y, int z) {
     const int64_t n = snode(g, x, y, z);
@@ -231,11 +232,23 @@ struct AoRow {
     e[2] = elem_index(n + 1, PLANES, 0);
     if (x == 0) e[0] = g.bc[0] == BC_PERIODIC ? elem_index(n + g.nx - 1, PLANES, 0) : e[1] + 2 * 32;
     if (x == g.nx - 1) e[2] = g.bc[1] == BC_PERIODIC ? elem_index(n - (g.nx - 1), PLANES, 0) : e[1] - 2 * 32;
+    dxm = (int)(e[0] - e[1]);
+    dxp = (int)(e[2] - e[1]);
+  }
+  // element offset of plane 0 of the slot S(x, t) from the node's own plane 0, in 32 bits (a z
+  // plane of storage holds fewer than 2^31 elements, checked at creation): slot pointers are the
+  // node's base pointer plus one 32-bit offset, one wide multiply-add per access.  nxs is a
+  // multiple of 32, so a y step moves nxs / 32 whole blocks of PLANES * 32 elements: nxs * PLANES
+  // elements (a z step nxs * ny * PLANES), products the whole grid shares.
+  template <int T, int PLANES>
+  __device__ __forceinline__ int rel0(const Geom& g) const {
+    const int dx = cx_of(T) < 0 ? dxm : (cx_of(T) > 0 ? dxp : 0);
+    return dx + cy_of(T) * (g.nxs * PLANES) + cz_of(T) * (g.nxs * g.ny * PLANES);
   }
   // element index of plane 0 of the slot S(x, t) (add the plane of t)
   template <int T, int PLANES>
   __device__ __forceinline__ int64_t slot0(const Geom& g) const {
-    return e[cx_of(T) + 1] + (int64_t)((cy_of(T) * g.nxs + cz_of(T) * (g.nxs * g.ny)) >> 5) * (PLANES * 32);
+    return e[cx_of(T) + 1] + (int64_t)(cy_of(T) * (g.nxs * PLANES) + cz_of(T) * (g.nxs * g.ny * PLANES));
   }
 };
 
@@ -300,6 +313,20 @@ struct PlainStore {  // FP64 or FP32: f^r and f^b planes [2][27][Ns]
   }
   template <typename R>
   __device__ __forceinline__ static R red_finish(R acc) { return acc; }
+  // by a node's base pointer p1 = A + e1 and a 32-bit element offset (fast rows)
+  template <typename R>
+  __device__ __forceinline__ void load_red_rel(const T* p1, int rel, int dir, int, const KConst<R>&, R& acc,
+                                               R& ft) const {
+    const R fr = (R)__ldcs(p1 + (rel + dir * 32));
+    ft = fr + (R)__ldcs(p1 + (rel + (27 + dir) * 32));
+    acc += fr;
+  }
+  template <typename R>
+  __device__ __forceinline__ void store_rel(T* p1, int rel, int dir, int, const KConst<R>&, R outr, R outb, R,
+                                            R) const {
+    __stcs(p1 + (rel + dir * 32), (T)outr);
+    __stcs(p1 + (rel + (27 + dir) * 32), (T)outb);
+  }
   template <typename R>
   __device__ __forceinline__ void store_at(int64_t e0, int dir, int, const KConst<R>&, R outr, R outb, R, R) const {
     __stcs(A + e0 + dir * 32, (T)outr);
@@ -415,6 +442,20 @@ struct PackedStore {
   }
   template <typename R>
   __device__ __forceinline__ static R red_finish(R acc) { return acc * R(1.0 / 65535.0); }
+  // by a node's base pointer p1 = A + e1 and a 32-bit element offset (fast rows)
+  template <typename R>
+  __device__ __forceinline__ void load_red_rel(const uint32_t* p1, int rel, int dir, int cls, const KConst<R>& K,
+                                               R& acc, R& ft) const {
+    float a = (float)acc;
+    ft = (R)decode_red(__ldcs(p1 + (rel + dir * 32)), (float)K.refB[cls], cls == 0 ? (float)K.dref[0] : 0.0f, a);
+    acc = (R)a;
+  }
+  template <typename R>
+  __device__ __forceinline__ void store_rel(uint32_t* p1, int rel, int dir, int cls, const KConst<R>& K, R, R,
+                                            R fstar, R q) const {
+    __stcs(p1 + (rel + dir * 32), encode((float)K.refB[cls], cls == 0 ? (float)K.dref[0] : 0.0f, (float)fstar,
+                                         (float)q));
+  }
   template <typename R>
   __device__ __forceinline__ void load_rb(int64_t node, int dir, int cls, const KConst<R>& K, R& fr, R& fb) const {
     R ft;
@@ -478,23 +519,24 @@ template <class Store, typename R>
 __device__ __forceinline__ void load_node_fast(const Store& st, const KConst<R>& K, const Geom& G, const AoRow& ar,
                                                int odd, R& rho_r, R ft[27]) {
   R acc = R(0);
+  const auto* p1 = st.A + ar.e[1];
   if (!odd) {
 #pragma unroll
-    for (int t = 0; t < 27; ++t) st.load_red_at(ar.e[1], t, speed2_of(t), K, acc, ft[t]);
+    for (int t = 0; t < 27; ++t) st.load_red_rel(p1, 0, t, speed2_of(t), K, acc, ft[t]);
   } else {
 #pragma unroll
     for (int t = 0; t < 27; ++t) {
-      int64_t e0;
+      int rel;
       switch (26 - t) {
-#define LBMK_CASE(k) case k: e0 = ar.slot0<k, Store::PLANES>(G); break;
+#define LBMK_CASE(k) case k: rel = ar.rel0<k, Store::PLANES>(G); break;
         LBMK_CASE(0) LBMK_CASE(1) LBMK_CASE(2) LBMK_CASE(3) LBMK_CASE(4) LBMK_CASE(5) LBMK_CASE(6)
         LBMK_CASE(7) LBMK_CASE(8) LBMK_CASE(9) LBMK_CASE(10) LBMK_CASE(11) LBMK_CASE(12) LBMK_CASE(13)
         LBMK_CASE(14) LBMK_CASE(15) LBMK_CASE(16) LBMK_CASE(17) LBMK_CASE(18) LBMK_CASE(19) LBMK_CASE(20)
         LBMK_CASE(21) LBMK_CASE(22) LBMK_CASE(23) LBMK_CASE(24) LBMK_CASE(25)
-        default: e0 = ar.slot0<26, Store::PLANES>(G); break;
+        default: rel = ar.rel0<26, Store::PLANES>(G); break;
 #undef LBMK_CASE
       }
-      st.load_red_at(e0, opp_of(t), speed2_of(t), K, acc, ft[t]);
+      st.load_red_rel(p1, rel, opp_of(t), speed2_of(t), K, acc, ft[t]);
     }
   }
   rho_r += Store::red_finish(acc);
@@ -866,8 +908,9 @@ __device__ __forceinline__ void emit(const Store& st, const KConst<R>& K, const 
   }
   const R outb = fstar - outr;
   if (FAST) {
-    if (!odd) st.store_at(ar.e[1], opp_of(T), speed2_of(T), K, outr, outb, fstar, q);
-    else st.store_at(ar.slot0<T, Store::PLANES>(G), T, speed2_of(T), K, outr, outb, fstar, q);
+    auto* p1 = st.A + ar.e[1];
+    if (!odd) st.store_rel(p1, 0, opp_of(T), speed2_of(T), K, outr, outb, fstar, q);
+    else st.store_rel(p1, ar.rel0<T, Store::PLANES>(G), T, speed2_of(T), K, outr, outb, fstar, q);
   } else if (!odd) {
     st.store(nm.base, opp_of(T), speed2_of(T), K, outr, outb, fstar, q);
   } else {

@@ -4,6 +4,61 @@
 
 namespace lbmk {
 
+// cuTensorMapEncodeTiled, taken from the driver through the runtime (no link against libcuda)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+static bool encode(EncodeTiledFn enc, CUtensorMap* m, CUtensorMapDataType type, int rank, void* base,
+                   const cuuint64_t* dims, const cuuint64_t* strides, const cuuint32_t* box) {
+  const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
+  return enc(m, type, (cuuint32_t)rank, base, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+// tensor maps of the pipelined compact pass 1: the totals as (word, plane, block, y, z + 1) and
+// the records as (4 x, y, z + 1) floats, over the whole storage including the ghost planes
+template <bool B>
+static bool density_maps(const CompactStore<B>& st, const Geom& G, DcMaps& M) {
+  const EncodeTiledFn enc = encode_tiled();
+  if (!enc) return false;
+  const cuuint64_t XC = (cuuint64_t)G.nxs / 32, ny = (cuuint64_t)G.ny, nzg = (cuuint64_t)G.nz + 2;
+  const cuuint64_t td[5] = {32, (cuuint64_t)CPLANES, XC, ny, nzg};
+  const cuuint64_t ts[4] = {64, 64 * (cuuint64_t)CPLANES, 64 * (cuuint64_t)CPLANES * XC,
+                            64 * (cuuint64_t)CPLANES * XC * ny};
+  const cuuint32_t brest[5] = {32, 1, 1, BY, BZ};
+  // the same totals as 8-byte words (224 per 32-node block of 28 planes): long rows for the boxes
+  const cuuint64_t wd[4] = {8 * (cuuint64_t)CPLANES, XC, ny, nzg};
+  const cuuint64_t ws[3] = {64 * (cuuint64_t)CPLANES, 64 * (cuuint64_t)CPLANES * XC, 64 * (cuuint64_t)CPLANES * XC * ny};
+  const cuuint32_t bgrp[4] = {72, 1, BY + 2, BZ}, beven[4] = {8 * (cuuint32_t)CPLANES, 1, BY, BZ};
+  const cuuint64_t rd[3] = {4 * (cuuint64_t)G.nxs, ny, nzg};
+  const cuuint64_t rs[2] = {16 * (cuuint64_t)G.nxs, 16 * (cuuint64_t)G.nxs * ny};
+  const cuuint32_t brec[3] = {4 * TX, TY, TZ};
+  return encode(enc, &M.rest, CU_TENSOR_MAP_DATA_TYPE_UINT16, 5, st.A, td, ts, brest) &&
+         encode(enc, &M.grp, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, st.A, wd, ws, bgrp) &&
+         encode(enc, &M.even, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, st.A, wd, ws, beven) &&
+         encode(enc, &M.rec, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, st.rec, rd, rs, brec);
+}
+
+static int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return n;
+}
+
 template <bool B>
 struct LaunchCompact {
   using Store = CompactStore<B>;
@@ -13,10 +68,32 @@ struct LaunchCompact {
                  G.Ns};
   }
   static KConst<float> kc(const Phys& P) { return make_kconst<float>(P); }
-  static cudaError_t density(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag, void*, int,
-                             cudaStream_t s) {
-    k_density_c<B><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(make(pop, G), G, kc(P), layout, static_cast<float2*>(dens),
-                                                          flag);
+  // pass 1: shape 3 the TMA pipeline (k_density_ct, fast rows; x faces that reflect and at least 3
+  // tiles along y and z, checked at creation) and the tiles next to the y/z faces; otherwise one
+  // block per 32x4x2 tile
+  static cudaError_t density(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag, void*,
+                             int shape, cudaStream_t s) {
+    const Store st = make(pop, G);
+    if (shape != 3) {
+      k_density_c<B><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(st, G, kc(P), layout, static_cast<float2*>(dens), flag,
+                                                            0);
+      return cudaGetLastError();
+    }
+    DcMaps M;
+    if (!density_maps(st, G, M)) return cudaErrorNotSupported;
+    using K0 = decltype(&k_density_ct<B, 0, DC_NG, DC_S, DC_MINB>);
+    const K0 kern[2] = {&k_density_ct<B, 0, DC_NG, DC_S, DC_MINB>, &k_density_ct<B, 1, DC_NG, DC_S, DC_MINB>};
+    static const bool attr =
+        cudaFuncSetAttribute(kern[0], cudaFuncAttributeMaxDynamicSharedMemorySize, DC_SMEM) == cudaSuccess &&
+        cudaFuncSetAttribute(kern[1], cudaFuncAttributeMaxDynamicSharedMemorySize, DC_SMEM) == cudaSuccess;
+    if (!attr) return cudaErrorInvalidValue;
+    const int ntx = (G.nx + BX - 1) / BX, nty = (G.ny + BY - 1) / BY, ntz = (G.nz + BZ - 1) / BZ;
+    const int ntiles = ntx * nty * ntz;
+    static const int nsm = sm_count();
+    const int per = DC_MINB * DC_NG;  // tiles a wave of blocks computes at once
+    const int grid = nsm > 0 && ntiles > per * nsm ? DC_MINB * nsm : (ntiles + DC_NG - 1) / DC_NG;
+    kern[layout ? 1 : 0]<<<grid, DC_THREADS, DC_SMEM, s>>>(st, G, kc(P), M, static_cast<float2*>(dens), flag, ntx,
+                                                          nty, ntiles);
     return cudaGetLastError();
   }
   static cudaError_t collide(void* pop, const Geom& G, const Phys& P, int odd, const void* dens, long long* counter,

@@ -47,7 +47,7 @@ def test_status_strings(lib):
 
 
 def _size(lib, shape, params, storage=1):
-    ps = binding._params_struct(params, storage)
+    ps = binding._params_struct(params, storage, block=params.get("block", 0))
     n = ctypes.c_size_t()
     rc = lib.lbm_workspace_size(*shape, ctypes.byref(ps), ctypes.byref(n))
     return rc, n.value
@@ -65,6 +65,10 @@ def test_workspace_size_scales_with_storage(lib):
 @pytest.mark.parametrize("bad", [
     dict(shape=(2, 8, 8)),
     dict(shape=(1200, 1200, 800)),                           # beyond the 2^30-node limit
+    dict(shape=(6400, 6400, 3)),                             # xy plane beyond 32-bit slot offsets
+    dict(block=4),                                           # pipelined pass 1 outside compact storage
+    dict(block=5),                                           # unknown block shape
+    dict(bc=(5, 5, 0, 0, 0, 0)),                             # halo faces on x
     dict(rho_r0=0.5),                                        # alpha_r < 0
     dict(nu_r=0.0),
     dict(beta=1.5),
@@ -81,7 +85,7 @@ def test_invalid_arguments_rejected(lib, bad):
     params = {**w["params"], **bad}
     rc, _ = _size(lib, shape, params)
     assert rc == -1
-    ps = binding._params_struct(params, 1)
+    ps = binding._params_struct(params, 1, block=params.get("block", 0))
     h = ctypes.c_void_p()
     assert lib.lbm_create(*shape, ctypes.byref(ps), ctypes.byref(h)) == -1
     assert not h.value
@@ -108,10 +112,28 @@ def test_null_handles(lib):
     (1, 3, True), (1, 4, False),                   # FP32: fused yes, pipelined (packed only) no
     (2, 3, True), (2, 4, True), (3, 4, True),      # packed: every variant
     (1, 5, False), (1, -1, False),
+    (4, 1, True), (4, 3, False), (5, 2, False),    # compact: one node per thread only
 ])
 def test_kernel_variant_validation(lib, storage, variant, ok):
     w = L.static_droplet(n=8, R=2.0)
     ps = binding._params_struct(w["params"], storage, variant=variant)
+    n = ctypes.c_size_t()
+    rc = lib.lbm_workspace_size(*w["shape"], ctypes.byref(ps), ctypes.byref(n))
+    assert (rc == 0) == ok
+
+
+@pytest.mark.parametrize("storage,xbc,block,ok", [
+    (4, L.FREESLIP, 4, True), (5, L.FREESLIP, 4, True),   # compact, free-slip x faces: pipelined pass 1
+    (4, L.PERIODIC, 4, False), (4, L.NOSLIP, 4, False),   # periodic / no-slip x faces: one block per tile
+    (4, L.FREESLIP, 1, True), (4, L.FREESLIP, 2, False), (5, L.PERIODIC, 3, False),
+    (2, L.FREESLIP, 4, False), (1, L.FREESLIP, 4, False),  # block 4 is a compact-storage density pass
+])
+def test_compact_block_validation(lib, storage, xbc, block, ok):
+    w = L.jet(nx=32, ny=16, nz=16, D=6.0)
+    bc = list(w["params"]["bc"])
+    bc[0] = bc[1] = xbc
+    params = {**w["params"], "bc": tuple(bc)}
+    ps = binding._params_struct(params, storage, block=block)
     n = ctypes.c_size_t()
     rc = lib.lbm_workspace_size(*w["shape"], ctypes.byref(ps), ctypes.byref(n))
     assert (rc == 0) == ok
