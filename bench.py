@@ -436,6 +436,7 @@ def main():
     torch.cuda.synchronize()
     with ClockSampler(dev.index) as clk:
         dt = timed(lat, args.steps)
+    clocks = clk.summary()
     dt_max = max_over_ranks(dt, ws, dev)
     mlups = ws * N * args.steps / dt_max / 1e6
     kps = lat.kernels_per_step
@@ -450,7 +451,9 @@ def main():
     if not args.no_fp32:
         lat32 = make("f32")
         lat32.step(args.warmup)
-        dt32 = max_over_ranks(timed(lat32, args.steps), ws, dev)
+        torch.cuda.synchronize()
+        with ClockSampler(dev.index) as clk32:
+            dt32 = max_over_ranks(timed(lat32, args.steps), ws, dev)
         variant32 = lat32.variant
         block32 = lat32.block
         ms32 = lat32.profile_step(min(200, args.steps))
@@ -459,7 +462,7 @@ def main():
         fp32 = {"value": ws * N * args.steps / dt32 / 1e6, "ms_per_step": dt32 / args.steps * 1e3,
                 "variant": variant32, "block": BLOCKS[block32], "pass1_ms": ms32[0], "collide_ms": ms32[1],
                 "collide_gbs": bytes32 / (ms32[1] * 1e-3) / 1e9, "collide_bytes_per_node": bytes32 // N,
-                "collide_traffic": profiled_traffic("f32", variant32)}
+                "collide_traffic": profiled_traffic("f32", variant32), "clocks": clk32.summary()}
 
     # ---- stated error against FP64 storage (outside the timed region) ----
     err = stated_error(pkg, [args.storage, "f32"]) if rank == 0 else None
@@ -509,8 +512,17 @@ def main():
                 "cpu_baseline": cpu,
                 "e2e": e2e,
                 "gpu_launches": kps * args.steps,
-                "clocks": clk.summary(),
+                "clocks": clocks,
                 "kernel_sources_sha": kernel_hash()}
+        if fp32 is not None:
+            # the step-time ratio against FP32 storage, and the same with each step time multiplied by
+            # the median SM clock sampled during its own timed region (clock drift between the runs)
+            c16, c32 = clocks.get("sm_mhz"), fp32["clocks"].get("sm_mhz")
+            t16, t32 = line["ms_per_step"], fp32["ms_per_step"]
+            line["vs_fp32"] = {"ratio": t32 / t16,
+                               "ms_x_mhz": [t16 * c16 if c16 else None, t32 * c32 if c32 else None],
+                               "ratio_clock_normalised": (t32 * c32) / (t16 * c16) if c16 and c32 else None,
+                               "target": 1.6}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
