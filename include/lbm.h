@@ -327,6 +327,19 @@ LBM_EXPORT void lbm_batch_free(lbm_batch* b);
  * Allocates and frees a small device buffer; synchronises. */
 LBM_EXPORT lbm_status lbm_measure_fp32_peak(void* cuda_stream, int packed, double* tflops);
 
+/* Self-test of the primitives of the TMA-pipelined density pass (a utility; the
+ * paper has no counterpart).  One block issues a tiled TMA copy of a 16 x 16
+ * box of a 32 x 32 FP32 tensor into shared memory, completing on one mbarrier
+ * with its byte count, and arms a second mbarrier for 16 bytes that no copy
+ * delivers.  *copy_ok = 1 if the copy completed with the expected values;
+ * *timed_out = 1 if the bounded wait on the second barrier gave up after
+ * wait_cycles SM clock cycles (1 .. 2e9) instead of spinning: the mechanism
+ * behind LBM_ETIMEOUT.  Runs on cuda_stream (NULL = legacy default stream),
+ * allocates and frees two small device buffers, synchronises.  LBM_EINVAL for
+ * NULL outputs or wait_cycles out of range; LBM_ECUDA if the driver offers no
+ * tensor-map encoder or a CUDA call fails. */
+LBM_EXPORT lbm_status lbm_selftest_tma(void* cuda_stream, long long wait_cycles, int* copy_ok, int* timed_out);
+
 /* Allocation-free diagnostics; the paper has no counterpart (it is an
  * interface for callers, not part of the method).  Reduces caller-owned device
  * fields rhoR, rhoB (N = nx*ny*nz doubles each, x fastest, e.g. filled by

@@ -11,7 +11,7 @@ operator, recolouring, streaming and the jet boundaries of Sec. IV.A.
 compiles the library.
 """
 from .lbm import (Batch, Lattice, LbmError, STORAGE, SYMBOLS, library, moment_matrix, selfcheck, diag_fields_static,  # noqa: F401,E501
-                  measure_fp32_peak,
+                  measure_fp32_peak, selftest_tma,
                   BC_PERIODIC, BC_NOSLIP, BC_FREESLIP, BC_INFLOW_WALL, BC_OUTFLOW, BC_HALO)
 from . import slabs  # noqa: F401
 from .build import build as build_library  # noqa: F401

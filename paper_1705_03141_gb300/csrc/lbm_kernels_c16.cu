@@ -1,6 +1,7 @@
 // Compact 16-bit storage (half or bfloat16 totals + one colour record per node), FP32 arithmetic.
 #include "lbm_compact.cuh"
 #include "lbm_launch.cuh"
+#include "../../include/lbm.h"
 
 namespace lbmk {
 
@@ -149,4 +150,73 @@ struct LaunchCompact {
 const KernelSet* kernels_c16() { return LaunchCompact<false>::table(); }
 const KernelSet* kernels_cbf16() { return LaunchCompact<true>::table(); }
 
+// Self-test of the pipeline's primitives: one tiled TMA copy of a 16 x 16 box of a 32 x 32 FP32
+// tensor (origin (8, 4)) completes on barrier a with its exact byte count, and barrier b, armed
+// for 16 bytes that no copy delivers, makes the bounded wait run out.  No copy is in flight when
+// the block leaves (the box has landed before the wait on b starts).
+static __global__ void k_tma_selftest(const __grid_constant__ CUtensorMap map, const float* __restrict__ src,
+                                      long long cycles, int* __restrict__ result) {
+  __shared__ __align__(128) float box[16 * 16];
+  __shared__ uint64_t a, b;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&a, 1);
+    mbar_init(&b, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&a, sizeof(box));
+    tma_load_2d(box, &map, &a, 8, 4);
+    mbar_arrive_expect_tx(&b, 16);
+  }
+  __syncthreads();
+  const bool landed = mbar_wait(&a, 0, kWaitCycles);
+  int ok = landed ? 1 : 0;
+  if (landed)
+    for (int i = tid; i < 16 * 16; i += blockDim.x) ok &= box[i] == src[(4 + i / 16) * 32 + 8 + i % 16] ? 1 : 0;
+  if (!ok) atomicAnd(result, 0);
+  if (landed && !mbar_wait(&b, 0, cycles)) atomicOr(result + 1, 1);
+}
+
 }  // namespace lbmk
+
+extern "C" lbm_status lbm_selftest_tma(void* cuda_stream, long long wait_cycles, int* copy_ok, int* timed_out) {
+  using namespace lbmk;
+  if (!copy_ok || !timed_out || wait_cycles < 1 || wait_cycles > kWaitCycles) return LBM_EINVAL;
+  const EncodeTiledFn enc = encode_tiled();
+  if (!enc) return LBM_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  float* src = nullptr;
+  int* res = nullptr;
+  if (cudaMalloc(&src, 32 * 32 * sizeof(float)) != cudaSuccess) return LBM_ENOMEM;
+  if (cudaMalloc(&res, 2 * sizeof(int)) != cudaSuccess) {
+    cudaFree(src);
+    return LBM_ENOMEM;
+  }
+  float host[32 * 32];
+  for (int i = 0; i < 32 * 32; ++i) host[i] = 0.25f * (float)i - 17.0f;
+  const int init[2] = {1, 0};
+  int out[2] = {0, 0};
+  lbm_status st = LBM_OK;
+  CUtensorMap map;
+  const cuuint64_t dims[2] = {32, 32}, strides[1] = {32 * sizeof(float)};
+  const cuuint32_t box[2] = {16, 16};
+  if (cudaMemcpyAsync(src, host, sizeof(host), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(res, init, sizeof(init), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    st = LBM_ECUDA;
+  else if (!encode(enc, &map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, src, dims, strides, box))
+    st = LBM_ECUDA;
+  if (st == LBM_OK) {
+    k_tma_selftest<<<1, 128, 0, s>>>(map, src, wait_cycles, res);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(out, res, sizeof(out), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      st = LBM_ECUDA;
+  }
+  cudaFree(src);
+  cudaFree(res);
+  *copy_ok = out[0];
+  *timed_out = out[1];
+  return st;
+}

@@ -28,7 +28,7 @@ SYMBOLS = ["lbm_workspace_size", "lbm_create", "lbm_init_fields", "lbm_set_inflo
            "lbm_diag", "lbm_get_populations", "lbm_set_populations", "lbm_profile_step", "lbm_set_stream", "lbm_synchronize", "lbm_time",
            "lbm_kernels_per_step", "lbm_last_error", "lbm_status_string", "lbm_moment_matrix", "lbm_selfcheck",
            "lbm_diag_fields_static", "lbm_autotune", "lbm_batch_create", "lbm_batch_step", "lbm_batch_synchronize",
-           "lbm_batch_free", "lbm_measure_fp32_peak", "lbm_kernel_variant", "lbm_kernel_block", "lbm_halo_bytes", "lbm_halo_pack",
+           "lbm_batch_free", "lbm_measure_fp32_peak", "lbm_selftest_tma", "lbm_kernel_variant", "lbm_kernel_block", "lbm_halo_bytes", "lbm_halo_pack",
            "lbm_halo_unpack", "lbm_step_pass", "lbm_free"]
 
 
@@ -100,6 +100,7 @@ def library():
         lib.lbm_batch_free.argtypes = [h]
         lib.lbm_batch_free.restype = None
         lib.lbm_measure_fp32_peak.argtypes = [vp, i, P(d)]
+        lib.lbm_selftest_tma.argtypes = [vp, ctypes.c_longlong, P(i), P(i)]
         lib.lbm_halo_bytes.argtypes = [h, i, P(ctypes.c_size_t)]
         lib.lbm_halo_pack.argtypes = [h, i, i, vp]
         lib.lbm_halo_unpack.argtypes = [h, i, i, vp]
@@ -160,6 +161,16 @@ def measure_fp32_peak(packed=False, stream=None):
     v = ctypes.c_double()
     _check(library().lbm_measure_fp32_peak(st.cuda_stream, int(bool(packed)), ctypes.byref(v)), None)
     return v.value
+
+
+def selftest_tma(wait_cycles=2_000_000, stream=None):
+    """(copy_ok, timed_out) of the TMA / bounded-mbarrier-wait self-test (include/lbm.h)."""
+    import torch
+
+    st = torch.cuda.current_stream() if stream is None else stream
+    ok, to = ctypes.c_int(), ctypes.c_int()
+    _check(library().lbm_selftest_tma(st.cuda_stream, int(wait_cycles), ctypes.byref(ok), ctypes.byref(to)), None)
+    return bool(ok.value), bool(to.value)
 
 
 def diag_fields_static(rho_r, rho_b, rho_r0, rho_b0, out=None, stream=None):

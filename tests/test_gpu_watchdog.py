@@ -51,3 +51,18 @@ def test_watchdog_reports_divergence(cuda, storage, variant):
     r, b, v = ok.macro()
     assert np.all(np.isfinite(r)) and np.all(np.isfinite(v))
     ok.close()
+
+
+def test_bounded_mbarrier_wait_runs_out(cuda):
+    """The waits of the TMA-pipelined density pass are bounded: a barrier armed for bytes that no
+    copy delivers makes the wait give up after the given clock budget (here about 1 ms) instead of
+    spinning, while a real tiled TMA copy on another barrier lands with the expected values.  The
+    context stays usable afterwards."""
+    copy_ok, timed_out = pkg.selftest_tma(wait_cycles=2_000_000)
+    assert copy_ok and timed_out
+    w = L.static_droplet(n=16, R=4.0)
+    lat = pkg.Lattice(w["shape"], w["params"], storage="c16")
+    lat.init_fields(*L.initial_fields(w))
+    lat.step(4)
+    lat.synchronize()
+    lat.close()
