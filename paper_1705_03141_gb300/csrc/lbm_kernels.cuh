@@ -1582,7 +1582,8 @@ __global__ void k_init(Store st, Geom G, const __grid_constant__ KConst<typename
   const double r = rr[n], b = rb[n];
   const double ar = K.alpha_r_d, ab = 8.0 / 27.0;
   const int64_t sn = snode(G, x, y, z);
-  for (int t = 0; t < 27; ++t) {
+#pragma unroll
+  for (int t = 0; t < 27; ++t) {  // the lattice constants fold at compile time
     const double w = weight_of(t);
     const double cu = cx_of(t) * u0 + cy_of(t) * u1 + cz_of(t) * u2;
     const double poly = w * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
