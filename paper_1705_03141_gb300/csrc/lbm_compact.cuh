@@ -204,41 +204,17 @@ __device__ __forceinline__ void fill_record_tile(const CompactStore<BF16>& st, c
 // loaded first and the record tile filled while they arrive; on a fast row the value arriving
 // along c_t left node x - c_t along c_t (x faces mirrored in the tile), elsewhere the emitter is
 // the owner of S(x, opp(t)) and its direction opp(stored direction) (records read directly)
-//
-// edge_tiles: a one-dimensional grid over the tiles that hold rows other than fast rows (the first
-// and last tile rows in y, and in z), writing those rows only: the complement of the pipelined
-// pass 1 below, which leaves them out (needs at least 3 tiles along y and z).
 template <bool BF16>
 __global__ void __launch_bounds__(NTHREADS, 3) k_density_c(CompactStore<BF16> st, const __grid_constant__ Geom G,
                                                            const __grid_constant__ KConst<float> K, int layout,
-                                                           float2* __restrict__ dens, int* __restrict__ flag,
-                                                           int edge_tiles) {
+                                                           float2* __restrict__ dens, int* __restrict__ flag) {
   __shared__ float4 rt[TILE];
-  int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * BZ;
-  if (edge_tiles) {
-    const int ntx = (G.nx + BX - 1) / BX, nty = (G.ny + BY - 1) / BY, ntz = (G.nz + BZ - 1) / BZ;
-    int b = blockIdx.x, kx, ky, kz;
-    if (b < 2 * ntx * ntz) {  // first / last tile row in y, every z
-      const int side = b / (ntx * ntz), rem = b % (ntx * ntz);
-      kx = rem % ntx;
-      kz = rem / ntx;
-      ky = side ? nty - 1 : 0;
-    } else {  // first / last tile row in z, the y tiles between
-      b -= 2 * ntx * ntz;
-      const int side = b / (ntx * (nty - 2)), rem = b % (ntx * (nty - 2));
-      kx = rem % ntx;
-      ky = 1 + rem / ntx;
-      kz = side ? ntz - 1 : 0;
-    }
-    x0 = kx * BX;
-    y0 = ky * BY;
-    z0 = kz * BZ;
-  }
+  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * BZ;
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
   const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
   const bool top = on_top(G, z);
   const bool fast = !top && fast_row(G, y, z);
-  const bool active = x < G.nx && y < G.ny && z < G.nz && !(edge_tiles && fast);
+  const bool active = x < G.nx && y < G.ny && z < G.nz;
   float f[27];
   if (active && !top) {
     if (fast) {

@@ -69,15 +69,13 @@ struct LaunchCompact {
                  G.Ns};
   }
   static KConst<float> kc(const Phys& P) { return make_kconst<float>(P); }
-  // pass 1: shape 3 the TMA pipeline (k_density_ct, fast rows; x faces that reflect and at least 3
-  // tiles along y and z, checked at creation) and the tiles next to the y/z faces; otherwise one
-  // block per 32x4x2 tile
+  // pass 1: shape 3 the TMA pipeline (k_density_ct; x faces that reflect and at least 3 tiles along
+  // y and z, checked at creation), otherwise one block per 32x4x2 tile
   static cudaError_t density(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag, void*,
                              int shape, cudaStream_t s) {
     const Store st = make(pop, G);
     if (shape != 3) {
-      k_density_c<B><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(st, G, kc(P), layout, static_cast<float2*>(dens), flag,
-                                                            0);
+      k_density_c<B><<<grid3(G), dim3(BX, BY, BZ), 0, s>>>(st, G, kc(P), layout, static_cast<float2*>(dens), flag);
       return cudaGetLastError();
     }
     DcMaps M;
