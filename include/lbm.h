@@ -212,7 +212,11 @@ LBM_EXPORT lbm_status lbm_set_inflow(lbm* h, double xc, double yc, double D, dou
  * steps has already been observed by a synchronising call.  Runs of 16 steps
  * replay a captured CUDA graph; with the environment variable LBM_NO_GRAPHS
  * set (read once per process) every step is launched directly instead (the
- * same kernels and results, for tools that do not follow graphs). */
+ * same kernels and results, for tools that do not follow graphs).  The
+ * collide-stream pass of the two-pass FP32-arithmetic kernels stages each
+ * block's (rho, phi) halo tile with one TMA copy; with LBM_NO_TMA set when a
+ * step is launched or captured, the tiles are loaded thread by thread (the
+ * same values, bitwise the same results). */
 LBM_EXPORT lbm_status lbm_step(lbm* h, int n);
 
 /* Macroscopic fields at the current time: rho_r, rho_b (N each) and

@@ -31,6 +31,7 @@
 #include <type_traits>
 
 #include "lbm_lattice.cuh"
+#include "lbm_tma.cuh"
 
 namespace lbmk {
 
@@ -43,11 +44,14 @@ constexpr int TILE = TX * TY * TZ;
 constexpr int NTHREADS = BX * BY * BZ;
 
 // Block shapes of the one-node density and collide-stream kernels (256 threads each; a warp is
-// always one 32-node x-row): 32 x BY x BZ nodes, and the (rho, phi) halo tile around them.
+// always one 32-node x-row): 32 x BY x BZ nodes, and the (rho, phi) halo tile around them.  The
+// collide-stream tile is TXT = 36 cells wide (x0-2 .. x0+33; columns 1..34 are read): a tiled
+// TMA copy must start on a 16-byte boundary, and x0 - 2 cells of 8 bytes is one.
 template <int BY_, int BZ_>
 struct Blk {
   static constexpr int BX = 32, BY = BY_, BZ = BZ_;
   static constexpr int TX = BX + 2, TY = BY + 2, TZ = BZ + 2, TILE = TX * TY * TZ;
+  static constexpr int TXT = BX + 4, TILET = TXT * TY * TZ;
   static constexpr int NT = BX * BY * BZ, NW = NT / 32;
   static_assert(NT == 256, "256-thread blocks");
 };
@@ -991,23 +995,88 @@ __global__ void __launch_bounds__(B::NT) k_density(Store st, Geom G,
   }
 }
 
+// The (rho, phi) halo tile of a collide-stream block through one tiled TMA copy.  The copy cannot
+// wrap around a periodic face, so blocks whose tile crosses one fill it with loads instead.
+template <class B>
+__device__ __forceinline__ bool tile_wraps(const Geom& G, int x0, int y0, int z0) {
+  return (x0 == 0 && G.bc[0] == BC_PERIODIC) || (x0 + B::BX >= G.nx && G.bc[1] == BC_PERIODIC) ||
+         (y0 == 0 && G.bc[2] == BC_PERIODIC) || (y0 + B::BY >= G.ny && G.bc[3] == BC_PERIODIC) ||
+         (z0 == 0 && G.bc[4] == BC_PERIODIC) || (z0 + B::BZ >= G.nz && G.bc[5] == BC_PERIODIC);
+}
+
+// In-box ranges of a TMA-copied tile (tile coordinates: column c is x = x0 - 2 + c, row r is
+// y = y0 - 1 + r, plane p is z = z0 - 1 + p).  Along z the box reaches the halo planes z = -1 and
+// z = nz on halo faces (the tensor covers both ghost planes); every other cell outside these ranges
+// is a mirror ghost of a wall, the inlet or the outflow plane: the in-box cell with its coordinates
+// clamped, as the loads of wrap_or_clamp give it.
+struct TileRange {
+  int cx0, cx1, cy0, cy1, cz0, cz1;
+  template <class B>
+  __device__ __forceinline__ void init(const Geom& G, int x0, int y0, int z0) {
+    const int zlo = G.bc[4] == BC_HALO ? -1 : 0, zhi = tile_zmax(G);
+    cx0 = max(2 - x0, 0);
+    cx1 = min(G.nx + 1 - x0, B::TXT - 1);
+    cy0 = max(1 - y0, 0);
+    cy1 = min(G.ny - y0, B::TY - 1);
+    cz0 = max(zlo + 1 - z0, 0);
+    cz1 = min(zhi + 1 - z0, B::TZ - 1);
+  }
+  template <class B>
+  __device__ __forceinline__ bool clamps() const {
+    return cx0 > 0 || cx1 < B::TXT - 1 || cy0 > 0 || cy1 < B::TY - 1 || cz0 > 0 || cz1 < B::TZ - 1;
+  }
+  template <class B>
+  __device__ __forceinline__ int src(int c, int r, int p) const {
+    return min(max(c, cx0), cx1) + B::TXT * (min(max(r, cy0), cy1) + B::TY * min(max(p, cz0), cz1));
+  }
+};
+
+// Replace the out-of-box cells of the tile by their clamped in-box cells: the out-of-box columns,
+// rows and planes in turn, each cell from the cell with all three coordinates clamped (never an
+// out-of-box cell itself, so the three loops need no ordering; corners are written twice with the
+// same value).
+template <class B, typename DT>
+__device__ __forceinline__ void tile_clamp_fix(DT* tile, const TileRange& tr, int tid) {
+  const int ncx = tr.cx0 + (B::TXT - 1 - tr.cx1), ncy = tr.cy0 + (B::TY - 1 - tr.cy1),
+            ncz = tr.cz0 + (B::TZ - 1 - tr.cz1);
+  for (int k = tid; k < ncx * B::TY * B::TZ; k += B::NT) {
+    const int j = k % ncx, rp = k / ncx;
+    const int c = j < tr.cx0 ? j : tr.cx1 + 1 + (j - tr.cx0), r = rp % B::TY, p = rp / B::TY;
+    tile[c + B::TXT * (r + B::TY * p)] = tile[tr.src<B>(c, r, p)];
+  }
+  for (int k = tid; k < ncy * B::TXT * B::TZ; k += B::NT) {
+    const int c = k % B::TXT, jp = k / B::TXT, j = jp % ncy, p = jp / ncy;
+    const int r = j < tr.cy0 ? j : tr.cy1 + 1 + (j - tr.cy0);
+    tile[c + B::TXT * (r + B::TY * p)] = tile[tr.src<B>(c, r, p)];
+  }
+  for (int k = tid; k < ncz * B::TXT * B::TY; k += B::NT) {
+    const int c = k % B::TXT, jr = k / B::TXT, r = jr % B::TY, j = jr / B::TY;
+    const int p = j < tr.cz0 ? j : tr.cz1 + 1 + (j - tr.cz0);
+    tile[c + B::TXT * (r + B::TY * p)] = tile[tr.src<B>(c, r, p)];
+  }
+}
+
 // pass 2: gradients + collision + perturbation + recolouring + in-place streaming.
 // counter[t & 1] holds the index t of the step (read by the inlet noise); the
 // kernel writes t + 1 into counter[(t + 1) & 1] for the next step, so a
 // captured graph of steps needs no parameter updates.  FUSED: (rho, phi) come
 // from the fixed-point accumulators of the previous step, and the kernel
 // accumulates those of the next step (fused_row, fused_node).
+// dmap, tma: with tma != 0 (two-pass kernels with an FP32 tile), the tensor map of the pass-1
+// field (rho, phi) as 8-byte cells over (x, y, z + 1), planes z = -1 .. nz, box 36 x TY x TZ; the
+// block's tile then arrives by one TMA copy while the population loads are in flight.
 template <class Store, int MINB, bool FUSED, class B = BlkDefault>
 __global__ void __launch_bounds__(B::NT, MINB)
     k_collide_stream(Store st, const __grid_constant__ Geom G,
                      const __grid_constant__ KConst<typename DensOf<Store>::real> K, int odd,
                      const typename DensOf<Store>::type* __restrict__ dens, long long* __restrict__ counter,
-                     const FusedIO io) {
+                     const FusedIO io, const __grid_constant__ CUtensorMap dmap, int tma) {
   using R = typename DensOf<Store>::real;  // compute type: FP64 for FP64 storage, FP32 otherwise
   using DT = typename DensOf<Store>::type;
-  __shared__ DT tile[B::TILE];
+  __shared__ __align__(128) DT tile[B::TILET];
   __shared__ float2 prow[FUSED ? B::NW * 9 * B::TX : 1];
   __shared__ int pfast[B::NW];
+  __shared__ uint64_t tbar;
 
   const int x0 = blockIdx.x * B::BX, y0 = blockIdx.y * B::BY, z0 = blockIdx.z * B::BZ;
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
@@ -1015,6 +1084,21 @@ __global__ void __launch_bounds__(B::NT, MINB)
   const int tid = threadIdx.x + B::BX * (threadIdx.y + B::BY * threadIdx.z);
   const long long step = counter[odd];
   if (tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) counter[odd ^ 1] = step + 1;
+
+  // block-uniform: the tile comes by TMA (no periodic face crossed)
+  bool via_tma = false;
+  if constexpr (!FUSED && std::is_same<DT, float2>::value) {
+    via_tma = tma != 0 && !tile_wraps<B>(G, x0, y0, z0);
+    if (via_tma) {
+      if (tid == 0) {
+        mbar_init(&tbar, 1);
+        mbar_fence_init();
+        mbar_arrive_expect_tx(&tbar, (uint32_t)(B::TILET * sizeof(DT)));
+        tma_load_3d(tile, &dmap, &tbar, x0 - 2, y0 - 1, z0);  // tensor plane z0 is z = z0 - 1
+      }
+      __syncthreads();  // the initialised barrier is visible to every thread before it waits
+    }
+  }
 
   R rho_r = R(0), ft[27];
   // a warp is one x-row of the block: the fast-row test is warp-uniform (the fused pass sums
@@ -1033,9 +1117,23 @@ __global__ void __launch_bounds__(B::NT, MINB)
     }
   }
 
-  // halo tile of (rho, phi): warp w fills rows w, w+8, w+16, ... of the TY*TZ rows of TX
-  // values; lanes cover x0-1 .. x0+30 and lanes 0..1 also x0+31, x0+32.
-  {
+  if (via_tma) {
+    // every thread waits for the copy (the barrier's phase completes with the copy's bytes), then
+    // the out-of-box cells get their mirror ghosts; a wait that runs out flags LBM_ETIMEOUT (the
+    // step's result is not used) and the copy's issuer waits once more before the block leaves
+    if (!mbar_wait(&tbar, 0)) {
+      atomicOr(io.flag, kFlagTimeout);
+      if (tid == 0) mbar_wait(&tbar, 0);
+    }
+    TileRange tr;
+    tr.init<B>(G, x0, y0, z0);
+    if (tr.clamps<B>()) {
+      tile_clamp_fix<B>(tile, tr, tid);
+      __syncthreads();
+    }
+  } else {
+    // halo tile of (rho, phi) by loads: warp w fills rows w, w+8, w+16, ... of the TY*TZ rows of
+    // columns 1..34 (x0-1 .. x0+32); lanes cover x0-1 .. x0+30 and lanes 0..1 also x0+31, x0+32.
     const int warp = tid >> 5, lane = threadIdx.x;
     const int xa = wrap_or_clamp(x0 + lane - 1, G.nx, G.bc[0], G.bc[1]);
     const int xb = wrap_or_clamp(x0 + lane + 31, G.nx, G.bc[0], G.bc[1]);
@@ -1052,11 +1150,11 @@ __global__ void __launch_bounds__(B::NT, MINB)
         const int cy = gy < G.ny ? gy : G.ny - 1, cz = gz <= tile_zmax(G) ? gz : tile_zmax(G);
         const int64_t rbase = (int64_t)G.nx * ((int64_t)cy + (int64_t)G.ny * cz);
         if constexpr (FUSED) {
-          tile[row * B::TX + lane] = fused_cell(io, rbase + cxa);
-          if (lane < B::TX - 32) tile[row * B::TX + 32 + lane] = fused_cell(io, rbase + cxb);
+          tile[row * B::TXT + 1 + lane] = fused_cell(io, rbase + cxa);
+          if (lane < B::TX - 32) tile[row * B::TXT + 33 + lane] = fused_cell(io, rbase + cxb);
         } else {
-          tile[row * B::TX + lane] = dens[rbase + cxa];
-          if (lane < B::TX - 32) tile[row * B::TX + 32 + lane] = dens[rbase + cxb];
+          tile[row * B::TXT + 1 + lane] = dens[rbase + cxa];
+          if (lane < B::TX - 32) tile[row * B::TXT + 33 + lane] = dens[rbase + cxb];
         }
       }
     }
@@ -1072,19 +1170,20 @@ __global__ void __launch_bounds__(B::NT, MINB)
           gx = gx < G.nx ? gx : G.nx - 1;
           gy = gy < G.ny ? gy : G.ny - 1;
           if (is_inlet(G, gx, gy, 0)) {
-            tile[c] = make_float2(rho_r0f, 1.0f);  // plane 0: z = -1 (z0 = 0) or z = 0 (z0 = 1)
-            if (z0 == 0) tile[c + B::TX * B::TY] = make_float2(rho_r0f, 1.0f);
+            const int ct = c % B::TX + 1 + B::TXT * (c / B::TX);  // the cell's index in the tile
+            tile[ct] = make_float2(rho_r0f, 1.0f);  // plane 0: z = -1 (z0 = 0) or z = 0 (z0 = 1)
+            if (z0 == 0) tile[ct + B::TXT * B::TY] = make_float2(rho_r0f, 1.0f);
           }
         }
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
   if (!FUSED && !active) return;
 
   if (active) {
     R gphi[3], grho[3];
-    tile_gradients<R, DT, B::TX, B::TY>(tile, threadIdx.x + 1, threadIdx.y + 1, threadIdx.z + 1, gphi, grho);
+    tile_gradients<R, DT, B::TXT, B::TY>(tile, threadIdx.x + 2, threadIdx.y + 1, threadIdx.z + 1, gphi, grho);
 
     R f[27];
     Recol<R> rc;

@@ -5,30 +5,6 @@
 
 namespace lbmk {
 
-// cuTensorMapEncodeTiled, taken from the driver through the runtime (no link against libcuda)
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-static EncodeTiledFn encode_tiled() {
-  static const EncodeTiledFn fn = [] {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      f = nullptr;
-    return reinterpret_cast<EncodeTiledFn>(f);
-  }();
-  return fn;
-}
-
-static bool encode(EncodeTiledFn enc, CUtensorMap* m, CUtensorMapDataType type, int rank, void* base,
-                   const cuuint64_t* dims, const cuuint64_t* strides, const cuuint32_t* box) {
-  const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
-  return enc(m, type, (cuuint32_t)rank, base, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-         CUDA_SUCCESS;
-}
-
 // tensor maps of the pipelined compact pass 1: the totals as (word, plane, block, y, z + 1) and
 // the records as (4 x, y, z + 1) floats, over the whole storage including the ghost planes
 template <bool B>

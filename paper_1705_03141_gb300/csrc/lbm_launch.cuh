@@ -1,7 +1,11 @@
 // Template launchers behind lbmk::KernelSet (internal).
 #pragma once
+#include <stdlib.h>
+#include <string.h>
+
 #include "lbm_dispatch.h"
 #include "lbm_kernels.cuh"
+#include "lbm_tma_host.h"
 
 namespace lbmk {
 
@@ -68,18 +72,39 @@ struct Launch {
     }
     return density_b<BlkDefault>(pop, G, P, layout, dens, flag, fix, s);
   }
+  // Tensor map of the pass-1 field for the TMA tile of k_collide_stream: 8-byte cells (rho, phi)
+  // over (x, y, z + 1), planes z = -1 .. nz (dens points at plane 0, one plane above the start of
+  // its buffer), box 36 x TY x TZ.  False where a TMA copy cannot be used: no driver entry point,
+  // odd nx (row strides must be multiples of 16 bytes) or a misaligned buffer; also where the
+  // environment variable LBM_NO_TMA is set when the launch is made (or captured into a graph):
+  // the tiles are then loaded as for boxes that cross a periodic face, with the same values.
+  template <class B>
+  static bool dens_map(const Geom& G, const void* dens, CUtensorMap* m) {
+    if (!std::is_same<DT, float2>::value || (G.nx & 1) || getenv("LBM_NO_TMA") != nullptr) return false;
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    char* base = const_cast<char*>(static_cast<const char*>(dens)) - (size_t)G.nx * G.ny * sizeof(DT);
+    if (reinterpret_cast<uintptr_t>(base) % 16 != 0) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)G.nx, (cuuint64_t)G.ny, (cuuint64_t)G.nz + 2};
+    const cuuint64_t strides[2] = {(cuuint64_t)G.nx * sizeof(DT), (cuuint64_t)G.nx * G.ny * sizeof(DT)};
+    const cuuint32_t box[3] = {(cuuint32_t)B::TXT, (cuuint32_t)B::TY, (cuuint32_t)B::TZ};
+    return encode(enc, m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, base, dims, strides, box);
+  }
   template <class B>
   static cudaError_t collide_b(void* pop, const Geom& G, const Phys& P, int odd, const void* dens, long long* counter,
                                bool fused_pass, const FusedIO& io, cudaStream_t s) {
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
     if constexpr (fused) {
       if (fused_pass) {
         k_collide_stream<Store, Tr::minb, true, B><<<grid3<B>(G), dim3(B::BX, B::BY, B::BZ), 0, s>>>(
-            Tr::make(pop, G), G, kc(P), odd, static_cast<const DT*>(dens), counter, io);
+            Tr::make(pop, G), G, kc(P), odd, static_cast<const DT*>(dens), counter, io, map, 0);
         return cudaGetLastError();
       }
     }
+    const int tma = dens_map<B>(G, dens, &map) ? 1 : 0;
     k_collide_stream<Store, Tr::minb, false, B><<<grid3<B>(G), dim3(B::BX, B::BY, B::BZ), 0, s>>>(
-        Tr::make(pop, G), G, kc(P), odd, static_cast<const DT*>(dens), counter, io);
+        Tr::make(pop, G), G, kc(P), odd, static_cast<const DT*>(dens), counter, io, map, tma);
     return cudaGetLastError();
   }
   static cudaError_t collide(void* pop, const Geom& G, const Phys& P, int odd, const void* dens, long long* counter,
