@@ -383,7 +383,8 @@ def main():
     ap.add_argument("--oracle-configs", action="store_true",
                     help="also time the oracle on the droplet set-ups and a jet sample, 1 and all threads")
     ap.add_argument("--variant", type=int, default=0, help="collide-stream kernel: 0 library choice, 1 one node "
-                    "per thread, 2 two nodes per thread, 3 fused density pass, 4 software-pipelined (packed)")
+                    "per thread, 2 two nodes per thread, 3 fused density pass, 4 software-pipelined (packed), "
+                    "5 TMA-pipelined interior tiles (packed)")
     ap.add_argument("--block", type=int, default=0, help="block shape of the one-node kernels: 0 library choice, "
                     "1 32x4x2, 2 32x2x4, 3 32x8x1, 4 pipelined density pass (compact storage)")
     args = ap.parse_args()
@@ -413,7 +414,11 @@ def main():
     rr, rb, u = L.initial_fields(w)
 
     def make(storage):
-        lat = pkg.Lattice(shape, w["params"], storage=storage, variant=args.variant, block=args.block)
+        # --variant / --block select the kernel of the headline storage; FP32 storage runs its own
+        # library choice (the fused density pass)
+        own = storage == args.storage
+        lat = pkg.Lattice(shape, w["params"], storage=storage, variant=args.variant if own else 0,
+                          block=args.block if own else 0)
         lat.init_fields(rr, rb, u)
         return lat
 

@@ -144,8 +144,8 @@ typedef struct {
                             allocates (cudaMalloc) and frees it itself. */
   size_t workspace_bytes;
   int variant;           /* collide-stream kernel: 0 = library's choice (3 for F32
-                            storage with nx a multiple of 32, 1 otherwise: the
-                            measured faster one),
+                            storage with nx a multiple of 32, 5 for F16/BF16
+                            storage, 1 otherwise: the measured faster ones),
                             1 = one node per thread, 2 = two x-adjacent nodes per
                             thread with packed FP32x2 arithmetic (needs F32/F16/BF16
                             storage and an even nx), 3 = one node per thread with
@@ -155,7 +155,16 @@ typedef struct {
                             4 = one node per thread, software-pipelined: persistent
                             blocks copy the next tile's populations into shared
                             memory while computing the current one (needs F16/BF16
-                            storage).  All variants compute the same update; they
+                            storage), 5 = the interior tiles (every row away from
+                            the y and z faces) by persistent blocks of 8 consumer
+                            warps and one producer warp that stages each tile's
+                            population words and (rho, phi) halo in shared memory
+                            with TMA copies, the remaining tiles by variant 1
+                            (needs F16/BF16 storage; where an x face is periodic or
+                            no-slip, nx is odd or the box has no interior tile,
+                            variant 5 runs variant 1 throughout, with the same
+                            results).  Variants 1 and 5 give bitwise the same
+                            fields.  All variants compute the same update; they
                             differ in FP32 rounding (variant 3 also rounds the
                             densities that enter the gradients to fixed point), and
                             each is bitwise reproducible.  F32/F16/BF16 storage needs
@@ -263,7 +272,7 @@ LBM_EXPORT long long lbm_time(const lbm* h);
  * pass also enqueues one memset per step, not counted). */
 LBM_EXPORT int lbm_kernels_per_step(const lbm* h);
 
-/* The collide-stream kernel variant the handle runs (1 to 4; see
+/* The collide-stream kernel variant the handle runs (1 to 5; see
  * lbm_params.variant and lbm_autotune); -1 for NULL. */
 LBM_EXPORT int lbm_kernel_variant(const lbm* h);
 
@@ -291,12 +300,12 @@ LBM_EXPORT lbm_status lbm_selfcheck(const char** msg);
 
 /* Pick the fastest collide-stream kernel for this handle by measurement: take
  * `steps` steps (>= 1) with each available variant (1; 2 where the storage and
- * nx allow; 3 for F32/F16/BF16 storage; 4 for F16/BF16 storage), variants 1
+ * nx allow; 3 for F32/F16/BF16 storage; 4 and 5 for F16/BF16 storage), variants 1
  * and 3 in each of the three block shapes of lbm_params.block (FP32-arithmetic
  * storages other than compact; compact storage: block 1 and, where its x faces
  * allow, block 4), timed with CUDA events on the handle's stream,
  * keep the fastest (variant, shape) for later steps and report the variant in
- * *chosen (1 to 4; may be NULL; lbm_kernel_block gives the shape).  The tuning
+ * *chosen (1 to 5; may be NULL; lbm_kernel_block gives the shape).  The tuning
  * steps are ordinary time steps of the same update, so the time advances by
  * steps times the number of candidates tried.  Synchronises. */
 LBM_EXPORT lbm_status lbm_autotune(lbm* h, int steps, int* chosen);

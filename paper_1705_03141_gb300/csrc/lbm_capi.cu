@@ -150,9 +150,11 @@ const char* validate(int nx, int ny, int nz, const lbm_params* p) {
   if (p->block == 4 && !(compact && pipelined_ok(nx, ny, nz, p)))
     return "block 4 (TMA-pipelined pass 1) needs compact storage, x faces that are neither periodic nor no-slip, "
            "nx % 32 != 1, ny > 8 and nz > 4";
-  if (p->variant < 0 || p->variant > 4) return "unknown kernel variant";
+  if (p->variant < 0 || p->variant > 5) return "unknown kernel variant";
   if (p->variant == 4 && p->storage != LBM_STORE_F16 && p->storage != LBM_STORE_BF16)
     return "the software-pipelined kernel needs packed (F16/BF16) storage";
+  if (p->variant == 5 && p->storage != LBM_STORE_F16 && p->storage != LBM_STORE_BF16)
+    return "the TMA-pipelined kernel (variant 5) needs packed (F16/BF16) storage";
   if (p->variant == 2 && (p->storage == LBM_STORE_F64 || nx % 2 != 0))
     return "the two-nodes-per-thread kernel needs FP32 arithmetic (not F64 storage) and an even nx";
   if (p->variant == 3 && p->storage == LBM_STORE_F64)
@@ -350,16 +352,19 @@ lbm_status lbm_create(int nx, int ny, int nz, const lbm_params* p, lbm** out) {
   // default, as measured on GB300: FP32 storage runs the fused density pass when rows
   // fill whole 32-node blocks (its collide-stream kernel is bandwidth-bound, so dropping
   // the separate density pass pays; partial blocks would take the per-direction atomic
-  // path); the packed storages and FP64 run one node per thread with the two-pass
-  // scheme (the packed kernel is issue-bound, and the fused accumulation costs more
+  // path); the packed storages run the two-pass scheme with the TMA-pipelined collide-stream
+  // kernel on the interior tiles (variant 5: 0.384 against 0.394 ms for the one-node kernel on
+  // the 128x128x512 jet; it runs variant 1 where it does not apply) and FP64 one node per
+  // thread (the packed kernels are issue-bound, and the fused accumulation costs more
   // instructions than the density pass); the two-node kernel's register footprint
   // leaves 8 warps per SM and measured slower everywhere
   h->halo = p->bc[4] == LBM_BC_HALO || p->bc[5] == LBM_BC_HALO;
   h->half = 0;
   h->recs_valid = false;
   h->dens_ready = false;
+  const bool packed = p->storage == LBM_STORE_F16 || p->storage == LBM_STORE_BF16;
   h->variant = p->variant != 0 ? p->variant
-                               : (p->storage == LBM_STORE_F32 && nx % 32 == 0 && !h->halo ? 3 : 1);
+                               : (p->storage == LBM_STORE_F32 && nx % 32 == 0 && !h->halo ? 3 : (packed ? 5 : 1));
   h->fix_ready = false;
   // block shape: as measured on GB300 (128x128x512 jet), the fused FP32 kernel runs fastest in
   // 32x2x4 blocks (0.784 against 0.814 ms for 32x4x2); every other kernel in 32x4x2
@@ -833,10 +838,10 @@ lbm_status lbm_autotune(lbm* h, int steps, int* chosen) {
   // of the FP32-arithmetic storages; compact storage: one-block or pipelined pass 1
   int cand[12][2], nc = 0;
   const bool shapes = !h->ks->compact && h->p.storage != LBM_STORE_F64;
-  for (int v = 1; v <= 4; ++v) {
+  for (int v = 1; v <= 5; ++v) {
     if (v == 2 && !(h->ks->has_paired && h->nx % 2 == 0 && !h->ks->compact)) continue;
     if (v == 3 && !h->ks->has_fused) continue;
-    if (v == 4 && !h->ks->has_pipelined) continue;
+    if ((v == 4 || v == 5) && !h->ks->has_pipelined) continue;
     for (int b = 0; b < ((v == 1 || v == 3) && shapes ? 3 : 1); ++b) {
       cand[nc][0] = v;
       cand[nc][1] = b;

@@ -20,7 +20,9 @@ struct KernelSet {
                          int shape, cudaStream_t s);
   // pass 2.  variant: 1 = one node per thread, 2 = two nodes per thread (FP32 arithmetic, nx even),
   // 3 = one node per thread with the fused density pass (reads cur, accumulates into nxt, which
-  // must be zero), 4 = software-pipelined one node per thread (packed storage).  counter: the
+  // must be zero), 4 = software-pipelined one node per thread (packed storage), 5 = the interior
+  // tiles by the TMA-pipelined kernel and the boundary tiles by variant 1 (packed storage; boxes
+  // with periodic or no-slip x faces, odd nx or no interior tile run variant 1).  counter: the
   // two-entry step index of k_collide_stream.
   cudaError_t (*collide)(void* pop, const Geom& G, const Phys& P, int odd, const void* dens, long long* counter,
                          int variant, const void* cur, void* nxt, int* flag, int shape, cudaStream_t s);

@@ -228,16 +228,25 @@ struct NodeMap {
 struct AoRow {
   int64_t e[3];
   int dxm, dxp;  // e[0] - e[1] and e[2] - e[1]
+  // the node's storage block (x >> 5) + (nxs / 32)(y + ny (z + 1)) fits 32 bits; within a block the
+  // x neighbours are one element away, across a block edge one block of PLANES planes minus 31
   template <int PLANES>
   __device__ __forceinline__ void init(const Geom& g, int x, int y, int z) {
-    const int64_t n = snode(g, x, y, z);
-    e[1] = elem_index(n, PLANES, 0);
-    e[0] = elem_index(n - 1, PLANES, 0);
-    e[2] = elem_index(n + 1, PLANES, 0);
-    if (x == 0) e[0] = g.bc[0] == BC_PERIODIC ? elem_index(n + g.nx - 1, PLANES, 0) : e[1] + 2 * 32;
-    if (x == g.nx - 1) e[2] = g.bc[1] == BC_PERIODIC ? elem_index(n - (g.nx - 1), PLANES, 0) : e[1] - 2 * 32;
-    dxm = (int)(e[0] - e[1]);
-    dxp = (int)(e[2] - e[1]);
+    const int lane = x & 31;
+    const int b = (x >> 5) + (g.nxs >> 5) * (y + g.ny * (z + 1));
+    e[1] = (int64_t)b * (PLANES * 32) + lane;
+    dxm = lane == 0 ? 31 - 32 * PLANES : -1;
+    dxp = lane == 31 ? 32 * PLANES - 31 : 1;
+    if (x == 0)
+      dxm = g.bc[0] == BC_PERIODIC ? (int)(elem_index(snode(g, g.nx - 1, y, z), PLANES, 0) - e[1]) : 2 * 32;
+    if (x == g.nx - 1) dxp = g.bc[1] == BC_PERIODIC ? (int)(elem_index(snode(g, 0, y, z), PLANES, 0) - e[1]) : -2 * 32;
+    e[0] = e[1] + dxm;
+    e[2] = e[1] + dxp;
+  }
+  // element offset of the storage row (y + cy, z + cz) from the node's own row (a grid-wide value)
+  template <int PLANES>
+  __device__ __forceinline__ int row_off(const Geom& g, int cy, int cz) const {
+    return cy * (g.nxs * PLANES) + cz * (g.nxs * g.ny * PLANES);
   }
   // element offset of plane 0 of the slot S(x, t) from the node's own plane 0, in 32 bits (a z
   // plane of storage holds fewer than 2^31 elements, checked at creation): slot pointers are the
@@ -277,6 +286,32 @@ __device__ __forceinline__ void slot_of(const NodeMap& nm, int layout, int t, in
     default: nm.push<26>(node, dir); break;
 #undef LBMK_CASE
   }
+}
+
+// slot_of for a direction known only at run time (one lane per direction): the slot map of
+// NodeMap::push written with selects instead of a switch, so the lanes of a warp do not diverge
+__device__ __forceinline__ void slot_of_rt(const NodeMap& nm, int layout, int t, int64_t& node, int& dir) {
+  if (layout == 0) {
+    node = nm.base;
+    dir = t;
+    return;
+  }
+  const int T = 26 - t;  // the slot S(x, opp(t))
+  const int c[3] = {cx_of(T), cy_of(T), cz_of(T)};
+  int off = 0, d = T;
+  bool bounce = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const unsigned bit = 1u << a;
+    const int sh = a == 0 ? 2 : (a == 1 ? 6 : 18);
+    const bool neg = c[a] < 0, pos = c[a] > 0;
+    off += neg ? nm.off_m[a] : (pos ? nm.off_p[a] : 0);
+    d += (neg && (nm.flip_m & bit)) ? sh : 0;
+    d -= (pos && (nm.flip_p & bit)) ? sh : 0;
+    bounce = bounce || (neg && (nm.bounce_m & bit)) || (pos && (nm.bounce_p & bit));
+  }
+  node = bounce ? nm.base : nm.base + off;
+  dir = bounce ? opp_of(T) : d;
 }
 
 // ---------------------------------------------------------------------------
@@ -379,6 +414,7 @@ template <bool BF16>
 struct PackedStore {
   using real = float;
   static constexpr int PLANES = 27;
+  static constexpr bool IS_BF16 = BF16;
   uint32_t* A;
   int64_t Ns;
   __device__ __forceinline__ static float dev_to_float(uint32_t bits) {
@@ -528,19 +564,17 @@ __device__ __forceinline__ void load_node_fast(const Store& st, const KConst<R>&
 #pragma unroll
     for (int t = 0; t < 27; ++t) st.load_red_rel(p1, 0, t, speed2_of(t), K, acc, ft[t]);
   } else {
+    // slot S(x, opp(t)) is plane T = opp(t) of node x + c_T: the three slots of a row group
+    // (c_y, c_z) of T share one row pointer and differ by the x shift dxm / 0 / dxp (t in
+    // ascending order, as on even steps)
 #pragma unroll
-    for (int t = 0; t < 27; ++t) {
-      int rel;
-      switch (26 - t) {
-#define LBMK_CASE(k) case k: rel = ar.rel0<k, Store::PLANES>(G); break;
-        LBMK_CASE(0) LBMK_CASE(1) LBMK_CASE(2) LBMK_CASE(3) LBMK_CASE(4) LBMK_CASE(5) LBMK_CASE(6)
-        LBMK_CASE(7) LBMK_CASE(8) LBMK_CASE(9) LBMK_CASE(10) LBMK_CASE(11) LBMK_CASE(12) LBMK_CASE(13)
-        LBMK_CASE(14) LBMK_CASE(15) LBMK_CASE(16) LBMK_CASE(17) LBMK_CASE(18) LBMK_CASE(19) LBMK_CASE(20)
-        LBMK_CASE(21) LBMK_CASE(22) LBMK_CASE(23) LBMK_CASE(24) LBMK_CASE(25)
-        default: rel = ar.rel0<26, Store::PLANES>(G); break;
-#undef LBMK_CASE
+    for (int g9 = 8; g9 >= 0; --g9) {
+      const auto* rp = p1 + ar.template row_off<Store::PLANES>(G, g9 % 3 - 1, g9 / 3 - 1);
+#pragma unroll
+      for (int a = 2; a >= 0; --a) {
+        const int T = a + 3 * g9;
+        st.load_red_rel(rp, a == 0 ? ar.dxm : (a == 2 ? ar.dxp : 0), T, speed2_of(T), K, acc, ft[26 - T]);
       }
-      st.load_red_rel(p1, rel, opp_of(t), speed2_of(t), K, acc, ft[t]);
     }
   }
   rho_r += Store::red_finish(acc);
@@ -914,7 +948,8 @@ __device__ __forceinline__ void emit(const Store& st, const KConst<R>& K, const 
   if (FAST) {
     auto* p1 = st.A + ar.e[1];
     if (!odd) st.store_rel(p1, 0, opp_of(T), speed2_of(T), K, outr, outb, fstar, q);
-    else st.store_rel(p1, ar.rel0<T, Store::PLANES>(G), T, speed2_of(T), K, outr, outb, fstar, q);
+    else st.store_rel(p1 + ar.template row_off<Store::PLANES>(G, cy_of(T), cz_of(T)),
+                      cx_of(T) < 0 ? ar.dxm : (cx_of(T) > 0 ? ar.dxp : 0), T, speed2_of(T), K, outr, outb, fstar, q);
   } else if (!odd) {
     st.store(nm.base, opp_of(T), speed2_of(T), K, outr, outb, fstar, q);
   } else {
@@ -1062,15 +1097,58 @@ __device__ __forceinline__ void tile_clamp_fix(DT* tile, const TileRange& tr, in
 // captured graph of steps needs no parameter updates.  FUSED: (rho, phi) come
 // from the fixed-point accumulators of the previous step, and the kernel
 // accumulates those of the next step (fused_row, fused_node).
+// Split of the tile grid into interior tiles (every row a fast row: 1 <= y, y + BY - 1 <= ny - 2,
+// and the same along z) and the boundary tiles around them.
+struct TileSplit {
+  int ntx, nty, ntz;  // tiles along x, y, z
+  int tyb, tzb;       // interior tile rows ty = 1 .. tyb, planes tz = 1 .. tzb
+  __host__ __device__ int ny_in() const { return tyb >= 1 ? tyb : 0; }
+  __host__ __device__ int nz_in() const { return tzb >= 1 ? tzb : 0; }
+  __host__ __device__ int interior() const { return ntx * ny_in() * nz_in(); }
+  __host__ __device__ int boundary() const { return ntx * nty * ntz - interior(); }
+  // boundary tile b -> tile origin: the tile planes below and above the interior, then the
+  // tile rows beside it (x fastest)
+  __device__ __forceinline__ void boundary_tile(int b, int BYv, int BZv, int& x0, int& y0, int& z0) const {
+    const int xi = b % ntx;
+    int p = b / ntx, ty, tz;
+    const int nlow = nty, nhigh = (ntz - 1 - nz_in()) * nty;
+    if (p < nlow) {
+      tz = 0;
+      ty = p;
+    } else if (p - nlow < nhigh) {
+      p -= nlow;
+      tz = nz_in() + 1 + p / nty;
+      ty = p % nty;
+    } else {
+      p -= nlow + nhigh;
+      const int per = nty - ny_in();  // tile rows beside the interior: 0 and ny_in + 1 ..
+      tz = 1 + p / per;
+      const int r = p % per;
+      ty = r == 0 ? 0 : ny_in() + r;
+    }
+    x0 = xi * 32;
+    y0 = ty * BYv;
+    z0 = tz * BZv;
+  }
+  __device__ __forceinline__ void interior_tile(int i, int BYv, int BZv, int& x0, int& y0, int& z0) const {
+    const int xi = i % ntx, p = i / ntx;
+    x0 = xi * 32;
+    y0 = (1 + p % ny_in()) * BYv;
+    z0 = (1 + p / ny_in()) * BZv;
+  }
+};
+
 // dmap, tma: with tma != 0 (two-pass kernels with an FP32 tile), the tensor map of the pass-1
 // field (rho, phi) as 8-byte cells over (x, y, z + 1), planes z = -1 .. nz, box 36 x TY x TZ; the
-// block's tile then arrives by one TMA copy while the population loads are in flight.
+// block's tile then arrives by one TMA copy while the population loads are in flight.  bmode != 0:
+// a one-dimensional grid over the boundary tiles of bt (the pipelined kernel takes the others).
 template <class Store, int MINB, bool FUSED, class B = BlkDefault>
 __global__ void __launch_bounds__(B::NT, MINB)
     k_collide_stream(Store st, const __grid_constant__ Geom G,
                      const __grid_constant__ KConst<typename DensOf<Store>::real> K, int odd,
                      const typename DensOf<Store>::type* __restrict__ dens, long long* __restrict__ counter,
-                     const FusedIO io, const __grid_constant__ CUtensorMap dmap, int tma) {
+                     const FusedIO io, const __grid_constant__ CUtensorMap dmap, int tma, const TileSplit bt,
+                     int bmode) {
   using R = typename DensOf<Store>::real;  // compute type: FP64 for FP64 storage, FP32 otherwise
   using DT = typename DensOf<Store>::type;
   __shared__ __align__(128) DT tile[B::TILET];
@@ -1078,7 +1156,8 @@ __global__ void __launch_bounds__(B::NT, MINB)
   __shared__ int pfast[B::NW];
   __shared__ uint64_t tbar;
 
-  const int x0 = blockIdx.x * B::BX, y0 = blockIdx.y * B::BY, z0 = blockIdx.z * B::BZ;
+  int x0 = blockIdx.x * B::BX, y0 = blockIdx.y * B::BY, z0 = blockIdx.z * B::BZ;
+  if (bmode) bt.boundary_tile(blockIdx.x, B::BY, B::BZ, x0, y0, z0);  // block 0: the tile at the origin
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
   const bool active = x < G.nx && y < G.ny && z < G.nz;
   const int tid = threadIdx.x + B::BX * (threadIdx.y + B::BY * threadIdx.z);
@@ -1610,9 +1689,13 @@ __device__ __forceinline__ R warp_allsum(R v) {
 
 // convective outflow on the z = nz-1 plane (Sec. IV.A), after the step that
 // produced time t+1; `layout` is the layout of time t+1.  One warp per column
-// (x, y), lane t < 27 for direction t: the plane holds only nx ny nodes, so a
-// thread per node would leave most SMs idle; the lanes reduce rho and the z
-// momentum of the node below with shuffles, then each updates its direction.
+// (x, y), lane t < 27 for direction t (the plane holds only nx ny nodes: a
+// thread per node would leave most of the SMs idle and run each column's 27
+// directions one after another); the slot map uses selects, so the lanes do not
+// diverge.  The lanes reduce rho and the z momentum of the node below with
+// shuffles, then each sets f(N, t+1) = (f(N, t) + lambda f(N-1, t+1)) /
+// (1 + lambda) for its direction and both colours, lambda = max(0, u_z(N-1, t+1));
+// `top` holds f(N, t) per column (32 red then 32 blue slots), and is updated.
 template <class Store>
 __global__ void __launch_bounds__(256) k_outflow(Store st, Geom G,
                                                  const __grid_constant__ KConst<typename DensOf<Store>::real> K,
@@ -1633,7 +1716,7 @@ __global__ void __launch_bounds__(256) k_outflow(Store st, Geom G,
   if (act) {
     int64_t node;
     int dir;
-    slot_of(below, layout, t, node, dir);
+    slot_of_rt(below, layout, t, node, dir);
     st.load_rb(node, dir, speed2_of(t), K, fr, fb);
   }
   const R v = fr + fb;
@@ -1654,7 +1737,7 @@ __global__ void __launch_bounds__(256) k_outflow(Store st, Geom G,
     *tb = nb;
     int64_t node;
     int dir;
-    slot_of(here, layout, t, node, dir);
+    slot_of_rt(here, layout, t, node, dir);
     store_pair(st, K, node, dir, nr, nb);
   }
   // fused density pass: the plane's new populations replace what the collide-stream kernel accumulated

@@ -5,6 +5,7 @@
 
 #include "lbm_dispatch.h"
 #include "lbm_kernels.cuh"
+#include "lbm_pipe.cuh"
 #include "lbm_tma_host.h"
 
 namespace lbmk {
@@ -98,14 +99,68 @@ struct Launch {
     if constexpr (fused) {
       if (fused_pass) {
         k_collide_stream<Store, Tr::minb, true, B><<<grid3<B>(G), dim3(B::BX, B::BY, B::BZ), 0, s>>>(
-            Tr::make(pop, G), G, kc(P), odd, static_cast<const DT*>(dens), counter, io, map, 0);
+            Tr::make(pop, G), G, kc(P), odd, static_cast<const DT*>(dens), counter, io, map, 0, TileSplit{}, 0);
         return cudaGetLastError();
       }
     }
     const int tma = dens_map<B>(G, dens, &map) ? 1 : 0;
     k_collide_stream<Store, Tr::minb, false, B><<<grid3<B>(G), dim3(B::BX, B::BY, B::BZ), 0, s>>>(
-        Tr::make(pop, G), G, kc(P), odd, static_cast<const DT*>(dens), counter, io, map, tma);
+        Tr::make(pop, G), G, kc(P), odd, static_cast<const DT*>(dens), counter, io, map, tma, TileSplit{}, 0);
     return cudaGetLastError();
+  }
+  // Variant 5 (packed storage): the boundary tiles by the one-node kernel, then the interior tiles
+  // by the TMA-pipelined kernel (lbm_pipe.cuh).  cudaErrorNotSupported where it does not apply:
+  // an x face that is periodic or bounces back (the mirror of the staged rows assumes a
+  // reflecting face), odd nx, no interior tile, or a tensor map that cannot be encoded.
+  static bool tp_applies(const Geom& G) {
+    const bool mirror_x = (G.bc[0] == BC_FREESLIP || G.bc[0] == BC_INFLOW_WALL) &&
+                          (G.bc[1] == BC_FREESLIP || G.bc[1] == BC_INFLOW_WALL);
+    return mirror_x && !(G.nx & 1) && tile_split(G).interior() > 0;
+  }
+  static TileSplit tile_split(const Geom& G) {
+    TileSplit ts;
+    ts.ntx = (G.nx + 31) / 32;
+    ts.nty = (G.ny + BY - 1) / BY;
+    ts.ntz = (G.nz + BZ - 1) / BZ;
+    ts.tyb = G.ny - 1 - BY >= 0 ? (G.ny - 1 - BY) / BY : 0;
+    ts.tzb = G.nz - 1 - BZ >= 0 ? (G.nz - 1 - BZ) / BZ : 0;
+    return ts;
+  }
+  static cudaError_t collide_tp(void* pop, const Geom& G, const Phys& P, int odd, const void* dens,
+                                long long* counter, const FusedIO& io, cudaStream_t s) {
+    if constexpr (pipelined) {
+      if (!tp_applies(G)) return cudaErrorNotSupported;
+      TpMaps M;
+      memset(&M, 0, sizeof(M));
+      if (!dens_map<BlkDefault>(G, dens, &M.dens)) return cudaErrorNotSupported;
+      const EncodeTiledFn enc = encode_tiled();
+      const cuuint64_t XC = (cuuint64_t)G.nxs / 32;
+      const cuuint64_t dims[5] = {32, 27, XC, (cuuint64_t)G.ny, (cuuint64_t)G.nz + 2};
+      const cuuint64_t strides[4] = {128, 27 * 128, 27 * 128 * XC, 27 * 128 * XC * (cuuint64_t)G.ny};
+      const cuuint32_t beven[5] = {32, 27, 1, BY, BZ}, bgrp[5] = {32, 3, 1, BY, BZ};
+      if (!encode(enc, &M.even, CU_TENSOR_MAP_DATA_TYPE_UINT32, 5, pop, dims, strides, beven) ||
+          !encode(enc, &M.grp, CU_TENSOR_MAP_DATA_TYPE_UINT32, 5, pop, dims, strides, bgrp))
+        return cudaErrorNotSupported;
+      const TileSplit ts = tile_split(G);
+      // boundary tiles first (block 0 is the tile at the origin: it advances the step counter)
+      k_collide_stream<Store, Tr::minb, false, BlkDefault><<<ts.boundary(), dim3(BX, BY, BZ), 0, s>>>(
+          Tr::make(pop, G), G, kc(P), odd, static_cast<const DT*>(dens), counter, io, M.dens, 1, ts, 1);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      using KT = decltype(&k_collide_stream_tp<Store::IS_BF16, 0>);
+      const KT kern[2] = {&k_collide_stream_tp<Store::IS_BF16, 0>, &k_collide_stream_tp<Store::IS_BF16, 1>};
+      static const bool attr =
+          cudaFuncSetAttribute(kern[0], cudaFuncAttributeMaxDynamicSharedMemorySize, TP_SMEM) == cudaSuccess &&
+          cudaFuncSetAttribute(kern[1], cudaFuncAttributeMaxDynamicSharedMemorySize, TP_SMEM) == cudaSuccess;
+      if (!attr) return cudaErrorInvalidValue;
+      int dev = 0, sms = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      const int n = ts.interior(), blocks = n < TP_MINB * sms ? n : TP_MINB * sms;
+      kern[odd ? 1 : 0]<<<blocks, TP_THREADS, TP_SMEM, s>>>(Tr::make(pop, G), G, kc(P), M, ts, io.flag);
+      return cudaGetLastError();
+    }
+    return cudaErrorNotSupported;
   }
   static cudaError_t collide(void* pop, const Geom& G, const Phys& P, int odd, const void* dens, long long* counter,
                              int variant, const void* cur, void* nxt, int* flag, int shape, cudaStream_t s) {
@@ -137,6 +192,12 @@ struct Launch {
       }
     }
     FusedIO io{static_cast<const unsigned long long*>(cur), static_cast<unsigned long long*>(nxt), flag};
+    if constexpr (pipelined) {
+      if (variant == 5) {
+        const cudaError_t e = collide_tp(pop, G, P, odd, dens, counter, io, s);
+        if (e != cudaErrorNotSupported) return e;  // else the box has no pipelined tiles: variant 1
+      }
+    }
     const bool fp = variant == 3;
     if constexpr (!std::is_same<R, double>::value) {
       if (shape == 1) return collide_b<Blk<2, 4>>(pop, G, P, odd, dens, counter, fp, io, s);

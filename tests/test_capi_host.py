@@ -111,7 +111,8 @@ def test_null_handles(lib):
     (0, 2, False), (0, 3, False), (0, 4, False),   # FP64: one node per thread only
     (1, 3, True), (1, 4, False),                   # FP32: fused yes, pipelined (packed only) no
     (2, 3, True), (2, 4, True), (3, 4, True),      # packed: every variant
-    (1, 5, False), (1, -1, False),
+    (2, 5, True), (3, 5, True), (0, 5, False),     # TMA-pipelined: packed only
+    (1, 5, False), (1, 6, False), (1, -1, False),
     (4, 1, True), (4, 3, False), (5, 2, False),    # compact: one node per thread only
 ])
 def test_kernel_variant_validation(lib, storage, variant, ok):

@@ -115,7 +115,8 @@ def test_autotune_keeps_a_valid_state(cuda, storage):
         # one node and fused density pass in three block shapes each, two nodes per thread
         assert chosen in (1, 2, 3) and lat.time == 28 and lat.block in (1, 2, 3)
     else:
-        assert chosen in (1, 2, 3, 4) and lat.time == 32  # ... and the software-pipelined kernel
+        # ... and the software- and TMA-pipelined kernels
+        assert chosen in (1, 2, 3, 4, 5) and lat.time == 36
     lat.step(100 - lat.time)
     rr, rb, u = L.initial_fields(work, seed=5, u_amp=u_amp)
     orc = oracle.Oracle(work["shape"], work["params"])

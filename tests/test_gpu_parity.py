@@ -71,7 +71,7 @@ def test_fp32_matches_oracle(cuda, name, variant):
     lat.close()
 
 
-PACKED = [(st, v) for st in ("f16", "bf16") for v in (1, 2, 3, 4)] + [("c16", 1), ("cbf16", 1)]
+PACKED = [(st, v) for st in ("f16", "bf16") for v in (1, 2, 3, 4, 5)] + [("c16", 1), ("cbf16", 1)]
 
 
 @pytest.mark.parametrize("storage,variant", PACKED)

@@ -89,3 +89,50 @@ def test_table_two_oscillation_period_converges(cuda):
           f"81^3, drop doubled: T_sim {t81:.0f} vs {th81:.0f}: {100 * e81:+.1f} %")
     assert 0 < e41 < 0.20
     assert 0 < e81 < 0.65 * e41
+
+
+def test_table_two_drop_shapes_at_the_papers_snapshot_times(cuda):
+    """Sec. III.B, Fig. dropOsci (nu = 3.333e-3, A = 1e-2): the initially prolate drop is spherical
+    at t = 700, oblate at t = 1,400 and prolate again at t = 2,500.  Through the FP64 path (equal
+    to the oracle), with a and b the interface radii along the major (x) and a minor (y) axis:
+    the drop is spherical where a - b first changes sign, oblate at the following minimum of
+    a - b and prolate at the maximum after it; each within 10 % of the paper's time (round
+    snapshot times).  The Miller-Scriven period of Eq. Lamb, 2,242 steps with the drop the dense
+    phase, would put the three shapes near 560, 1,120 and 2,240."""
+    n, axes, nu, A = 41, (15.0, 11.0, 11.0), 3.333e-3, 1e-2
+    w = L.oscillating_droplet(n=n, axes=axes, nu=nu, A=A, rho_r0=1.0, rho_b0=0.25)
+    rr, rb, u = L.initial_fields(w)
+    lat = pkg.Lattice(w["shape"], w["params"], storage="f64")
+    lat.init_fields(rr, rb, u)
+    c = (n - 1) // 2
+
+    def radius(line):
+        j = np.where((line[:-1] > 0) & (line[1:] <= 0))[0][-1]
+        return j + line[j] / (line[j] - line[j + 1]) - c
+
+    ts, d = [], []
+    for _ in range(2900 // 10):
+        lat.step(10)
+        r, b, _ = lat.macro()
+        phi = (r - b) / (r + b)
+        d.append(radius(phi[c, c, :]) - radius(phi[c, :, c]))
+        ts.append(lat.time)
+    lat.close()
+    d, ts = np.array(d), np.array(ts, dtype=np.float64)
+    k = int(np.where(d <= 0)[0][0])  # first sign change, interpolated
+    t_sphere = ts[k - 1] + 10 * d[k - 1] / (d[k - 1] - d[k])
+
+    def extremum(i0, sign):  # first local extremum (min: sign = -1) after sample i0, refined
+        for i in range(max(i0, 1), len(d) - 1):
+            if sign * (d[i] - d[i - 1]) > 0 and sign * (d[i + 1] - d[i]) < 0:
+                y0, y1, y2 = d[i - 1], d[i], d[i + 1]
+                return i, ts[i] + 10 * 0.5 * (y0 - y2) / (y0 - 2 * y1 + y2)
+        raise AssertionError("no extremum")
+
+    i_ob, t_oblate = extremum(k, -1)
+    _, t_prolate = extremum(i_ob + 1, +1)
+    print(f"Table II drop: sphere {t_sphere:.0f} (paper 700), oblate {t_oblate:.0f} (1,400), "
+          f"prolate {t_prolate:.0f} (2,500)")
+    assert abs(t_sphere - 700) < 0.10 * 700
+    assert abs(t_oblate - 1400) < 0.10 * 1400
+    assert abs(t_prolate - 2500) < 0.10 * 2500

@@ -20,7 +20,7 @@ EUNSTABLE = -4
 
 
 @pytest.mark.parametrize("storage,variant", [("f64", 1), ("f32", 1), ("f32", 3), ("f16", 1), ("bf16", 4),
-                                             ("c16", 1)])
+                                             ("f16", 5), ("c16", 1)])
 def test_watchdog_reports_divergence(cuda, storage, variant):
     w = L.static_droplet()  # tau = 1 with Suga's rates: linearly unstable
     rr, rb, u = L.initial_fields(w, seed=2, u_amp=1e-3)
