@@ -68,7 +68,8 @@ def peaks():
 
 
 KERNEL_SOURCES = ("lbm_f2.cuh", "lbm_kernels.cuh", "lbm_kernels_f16.cu", "lbm_kernels_f32.cu", "lbm_kernels_f64.cu",
-                  "lbm_lattice.cuh", "lbm_launch.cuh", "lbm_compact.cuh", "lbm_kernels_c16.cu", "lbm_tma.cuh")
+                  "lbm_lattice.cuh", "lbm_launch.cuh", "lbm_compact.cuh", "lbm_kernels_c16.cu", "lbm_tma.cuh",
+                  "lbm_pipe.cuh")
 
 
 def kernel_hash():
@@ -81,7 +82,7 @@ def kernel_hash():
 
 
 def profile_name(storage, variant):
-    return f"collide_stream{ {3: '_fused', 4: '_pipelined'}.get(variant, '') }_jet_{storage}.md"
+    return f"collide_stream{ {3: '_fused', 4: '_pipelined', 5: '_tma_pipelined'}.get(variant, '') }_jet_{storage}.md"
 
 
 KERNEL_REGEX = {"c16": "k_collide_stream_c", "cbf16": "k_collide_stream_c"}

@@ -220,16 +220,20 @@ void drop_graphs(lbm* h) {
     }
 }
 
+// variants with the fused density pass (no pass 1; fixed-point accumulators between steps)
+bool fused_variant(const lbm* h) { return h->variant == 3; }
+
 // enqueue one time step (the step with index t) on stream s; skip_density: the (rho, phi)
 // field already holds the state's densities (first step of compact storage after an upload)
 lbm_status enqueue_step(lbm* h, long long t, cudaStream_t s, bool skip_density = false) {
   const int layout = (int)(t & 1);
   const bool outflow = h->p.bc[5] == LBM_BC_OUTFLOW;
-  if (h->variant == 3) {
+  if (fused_variant(h)) {
     // fused density pass: no pass 1; the accumulators of t+1 start from zero
     unsigned long long *cur = h->fix[layout], *nxt = h->fix[layout ^ 1];
     LBM_CUDA(h, cudaMemsetAsync(nxt, 0, sizeof(unsigned long long) * (size_t)h->N, s));
-    LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, 3, cur, nxt, h->flag, h->shape, s));
+    LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->variant, cur, nxt, h->flag,
+                               h->shape, s));
     if (outflow) LBM_CUDA(h, h->ks->outflow(h->pop, h->G, h->P, layout ^ 1, h->top, nxt, s));
     return LBM_OK;
   }
@@ -243,7 +247,7 @@ lbm_status enqueue_step(lbm* h, long long t, cudaStream_t s, bool skip_density =
 
 // before fused steps from a state the fused pass did not produce: fill the accumulators of step t
 lbm_status ensure_fix(lbm* h, cudaStream_t s) {
-  if (h->variant != 3 || h->fix_ready) return LBM_OK;
+  if (!fused_variant(h) || h->fix_ready) return LBM_OK;
   LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, (int)(h->t & 1), h->dens, h->flag, h->fix[h->t & 1], h->shape, s));
   h->fix_ready = true;
   return LBM_OK;
@@ -698,7 +702,7 @@ lbm_status lbm_profile_step(lbm* h, int n, double* ms_out) {
       break;
     }
   if (st == LBM_OK) st = ensure_fix(h, h->stream);
-  const bool fused = h->variant == 3;
+  const bool fused = fused_variant(h);
   if (!fused) h->fix_ready = false;
   for (int k = 0; st == LBM_OK && k < n; ++k) {
     const long long t = h->t;
@@ -760,7 +764,9 @@ long long lbm_time(const lbm* h) { return h ? h->t : -1; }
 
 int lbm_kernels_per_step(const lbm* h) {
   if (!h) return -1;
-  return (h->variant == 3 ? 1 : 2) + (h->p.bc[5] == LBM_BC_OUTFLOW ? 1 : 0);
+  // variant 5 launches two collide-stream kernels (boundary and interior tiles) where it applies
+  const bool two = h->variant == 5 && lbmk::pipelined_tiles(h->G);
+  return (fused_variant(h) ? 1 : 2) + (two ? 1 : 0) + (h->p.bc[5] == LBM_BC_OUTFLOW ? 1 : 0);
 }
 
 int lbm_kernel_variant(const lbm* h) { return h ? h->variant : -1; }
@@ -904,7 +910,7 @@ lbm_status lbm_step_pass(lbm* h, int pass) {
       h->half = 1;
       return LBM_OK;
     }
-    if (h->variant == 3) {
+    if (fused_variant(h)) {
       lbm_status st = ensure_fix(h, s);
       if (st != LBM_OK) return st;
       LBM_CUDA(h, cudaMemsetAsync(h->fix[layout ^ 1], 0, sizeof(unsigned long long) * (size_t)h->N, s));
@@ -915,7 +921,7 @@ lbm_status lbm_step_pass(lbm* h, int pass) {
     h->half = 1;
     return LBM_OK;
   }
-  const bool fused = h->variant == 3;
+  const bool fused = fused_variant(h);
   LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->variant,
                              fused ? h->fix[layout] : nullptr, fused ? h->fix[layout ^ 1] : nullptr, h->flag, h->shape,
                              s));

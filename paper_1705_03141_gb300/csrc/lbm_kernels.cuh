@@ -1138,6 +1138,24 @@ struct TileSplit {
   }
 };
 
+// the tile split of the default 32 x BY x BZ blocks, and whether the TMA-pipelined kernel
+// (variant 5) takes the interior tiles: reflecting x faces (the staged rows mirror there),
+// even nx (8-byte density cells in 16-byte rows) and at least one interior tile
+inline TileSplit default_tile_split(const Geom& G) {
+  TileSplit ts;
+  ts.ntx = (G.nx + 31) / 32;
+  ts.nty = (G.ny + BY - 1) / BY;
+  ts.ntz = (G.nz + BZ - 1) / BZ;
+  ts.tyb = G.ny - 1 - BY >= 0 ? (G.ny - 1 - BY) / BY : 0;
+  ts.tzb = G.nz - 1 - BZ >= 0 ? (G.nz - 1 - BZ) / BZ : 0;
+  return ts;
+}
+inline bool pipelined_tiles(const Geom& G) {
+  const bool mirror_x = (G.bc[0] == BC_FREESLIP || G.bc[0] == BC_INFLOW_WALL) &&
+                        (G.bc[1] == BC_FREESLIP || G.bc[1] == BC_INFLOW_WALL);
+  return mirror_x && !(G.nx & 1) && default_tile_split(G).interior() > 0;
+}
+
 // dmap, tma: with tma != 0 (two-pass kernels with an FP32 tile), the tensor map of the pass-1
 // field (rho, phi) as 8-byte cells over (x, y, z + 1), planes z = -1 .. nz, box 36 x TY x TZ; the
 // block's tile then arrives by one TMA copy while the population loads are in flight.  bmode != 0:

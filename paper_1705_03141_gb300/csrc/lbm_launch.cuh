@@ -112,20 +112,8 @@ struct Launch {
   // by the TMA-pipelined kernel (lbm_pipe.cuh).  cudaErrorNotSupported where it does not apply:
   // an x face that is periodic or bounces back (the mirror of the staged rows assumes a
   // reflecting face), odd nx, no interior tile, or a tensor map that cannot be encoded.
-  static bool tp_applies(const Geom& G) {
-    const bool mirror_x = (G.bc[0] == BC_FREESLIP || G.bc[0] == BC_INFLOW_WALL) &&
-                          (G.bc[1] == BC_FREESLIP || G.bc[1] == BC_INFLOW_WALL);
-    return mirror_x && !(G.nx & 1) && tile_split(G).interior() > 0;
-  }
-  static TileSplit tile_split(const Geom& G) {
-    TileSplit ts;
-    ts.ntx = (G.nx + 31) / 32;
-    ts.nty = (G.ny + BY - 1) / BY;
-    ts.ntz = (G.nz + BZ - 1) / BZ;
-    ts.tyb = G.ny - 1 - BY >= 0 ? (G.ny - 1 - BY) / BY : 0;
-    ts.tzb = G.nz - 1 - BZ >= 0 ? (G.nz - 1 - BZ) / BZ : 0;
-    return ts;
-  }
+  static bool tp_applies(const Geom& G) { return pipelined_tiles(G); }
+  static TileSplit tile_split(const Geom& G) { return default_tile_split(G); }
   static cudaError_t collide_tp(void* pop, const Geom& G, const Phys& P, int odd, const void* dens,
                                 long long* counter, const FusedIO& io, cudaStream_t s) {
     if constexpr (pipelined) {
