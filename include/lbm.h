@@ -269,8 +269,16 @@ LBM_EXPORT lbm_status lbm_synchronize(lbm* h);
 LBM_EXPORT long long lbm_time(const lbm* h);
 
 /* Number of kernel launches one lbm_step(h, 1) enqueues (the fused density
- * pass also enqueues one memset per step, not counted). */
+ * pass also enqueues one memset per step, not counted; longer runs launch the
+ * outflow kernel once per run: lbm_launch_count counts exactly). */
 LBM_EXPORT int lbm_kernels_per_step(const lbm* h);
+
+/* Kernel launches the handle's stepping calls (lbm_step, lbm_autotune, lbm_batch_step) have
+ * enqueued since lbm_create: each CUDA-graph replay counts the kernels the graph holds.  The
+ * fused density pass's memset is not a kernel and is not counted.  Runs of two-pass steps with
+ * an outflow face launch the outflow kernel once, after their last step (the outflow of each
+ * earlier step runs at the start of the next step's density pass).  -1 for NULL. */
+LBM_EXPORT long long lbm_launch_count(const lbm* h);
 
 /* The collide-stream kernel variant the handle runs (1 to 5; see
  * lbm_params.variant and lbm_autotune); -1 for NULL. */

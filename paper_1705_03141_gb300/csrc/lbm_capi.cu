@@ -53,6 +53,8 @@ struct lbm {
   cudaStream_t stream;
   cudaStream_t cap_stream;
   cudaGraphExec_t graph[2];  // kGraphSteps steps starting at an even / odd step
+  long long graph_kernels[2];  // kernel launches one replay of graph[k] makes
+  long long launches;          // kernel launches of this handle's steps so far (lbm_launch_count)
   long long t;
   bool unstable;
   bool timed_out;  // a bounded device-side wait ran out (flag bit kFlagTimeout)
@@ -224,12 +226,18 @@ void drop_graphs(lbm* h) {
 bool fused_variant(const lbm* h) { return h->variant == 3; }
 
 // enqueue one time step (the step with index t) on stream s; skip_density: the (rho, phi)
-// field already holds the state's densities (first step of compact storage after an upload)
-lbm_status enqueue_step(lbm* h, long long t, cudaStream_t s, bool skip_density = false) {
+// field already holds the state's densities (first step of compact storage after an upload).
+// Runs of two-pass steps with an outflow face (enqueue_run): fold, pass 1 first completes the
+// step before with its convective outflow; last = false, the outflow kernel is left to the
+// folding pass 1 of the next step.
+lbm_status enqueue_step(lbm* h, long long t, cudaStream_t s, bool skip_density = false, bool fold = false,
+                        bool last = true) {
   const int layout = (int)(t & 1);
   const bool outflow = h->p.bc[5] == LBM_BC_OUTFLOW;
+  const long long ck = (h->variant == 5 && lbmk::pipelined_tiles(h->G)) ? 2 : 1;  // collide-stream launches
   if (fused_variant(h)) {
     // fused density pass: no pass 1; the accumulators of t+1 start from zero
+    h->launches += ck + (outflow ? 1 : 0);
     unsigned long long *cur = h->fix[layout], *nxt = h->fix[layout ^ 1];
     LBM_CUDA(h, cudaMemsetAsync(nxt, 0, sizeof(unsigned long long) * (size_t)h->N, s));
     LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->variant, cur, nxt, h->flag,
@@ -238,10 +246,26 @@ lbm_status enqueue_step(lbm* h, long long t, cudaStream_t s, bool skip_density =
     return LBM_OK;
   }
   h->fix_ready = false;  // steps without the fused pass leave its accumulators behind
-  if (!skip_density) LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, nullptr, h->shape, s));
+  h->launches += (skip_density ? 0 : 1) + ck + (outflow && last ? 1 : 0);
+  if (!skip_density) {
+    if (fold) LBM_CUDA(h, h->ks->density_fold(h->pop, h->G, h->P, layout, h->dens, h->flag, h->top, h->shape, s));
+    else LBM_CUDA(h, h->ks->density(h->pop, h->G, h->P, layout, h->dens, h->flag, nullptr, h->shape, s));
+  }
   LBM_CUDA(h, h->ks->collide(h->pop, h->G, h->P, layout, h->dens, h->counter, h->variant, nullptr, nullptr,
                              h->flag, h->shape, s));
-  if (outflow) LBM_CUDA(h, h->ks->outflow(h->pop, h->G, h->P, layout ^ 1, h->top, nullptr, s));
+  if (outflow && last) LBM_CUDA(h, h->ks->outflow(h->pop, h->G, h->P, layout ^ 1, h->top, nullptr, s));
+  return LBM_OK;
+}
+
+// n >= 1 steps from step t0: with an outflow face, the two-pass schemes launch the outflow
+// kernel only after the last step; each earlier step's outflow runs at the start of the next
+// step's pass 1 (the same arithmetic), so the state after the run is the same
+lbm_status enqueue_run(lbm* h, long long t0, int n, cudaStream_t s) {
+  const bool fold = h->p.bc[5] == LBM_BC_OUTFLOW && !fused_variant(h) && h->ks->density_fold != nullptr;
+  for (int k = 0; k < n; ++k) {
+    lbm_status st = enqueue_step(h, t0 + k, s, false, fold && k > 0, !fold || k == n - 1);
+    if (st != LBM_OK) return st;
+  }
   return LBM_OK;
 }
 
@@ -263,7 +287,10 @@ lbm_status build_graph(lbm* h, int parity) {
   cudaGraph_t g = nullptr;
   LBM_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   lbm_status st = LBM_OK;
-  for (int k = 0; k < kGraphSteps && st == LBM_OK; ++k) st = enqueue_step(h, parity + k, h->cap_stream);
+  const long long before = h->launches;  // captured, not launched: counted per replay
+  st = enqueue_run(h, parity, kGraphSteps, h->cap_stream);
+  h->graph_kernels[parity] = h->launches - before;
+  h->launches = before;
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
   if (st != LBM_OK) {
     if (g) cudaGraphDestroy(g);
@@ -557,12 +584,13 @@ lbm_status lbm_step(lbm* h, int n) {
     for (; k + kGraphSteps <= n; k += kGraphSteps) {
       LBM_CUDA(h, cudaGraphLaunch(h->graph[parity], h->stream));
       h->t += kGraphSteps;
+      h->launches += h->graph_kernels[parity];
     }
   }
-  for (; k < n; ++k) {
-    lbm_status st = enqueue_step(h, h->t, h->stream);
+  if (k < n) {
+    lbm_status st = enqueue_run(h, h->t, n - k, h->stream);
     if (st != LBM_OK) return st;
-    h->t += 1;
+    h->t += n - k;
   }
   return LBM_OK;
 }
@@ -771,6 +799,8 @@ int lbm_kernels_per_step(const lbm* h) {
 
 int lbm_kernel_variant(const lbm* h) { return h ? h->variant : -1; }
 
+long long lbm_launch_count(const lbm* h) { return h ? h->launches : -1; }
+
 int lbm_kernel_block(const lbm* h) { return h ? h->shape + 1 : -1; }
 
 const char* lbm_last_error(const lbm* h) { return h ? h->err.c_str() : "NULL handle"; }
@@ -875,10 +905,8 @@ lbm_status lbm_autotune(lbm* h, int steps, int* chosen) {
     // direct launches: every kernel timed the same way, no graph capture in between
     if (st == LBM_OK && cudaEventRecord(e0, h->stream) != cudaSuccess)
       st = fail(h, LBM_ECUDA, "cudaEventRecord failed");
-    for (int k = 0; k < steps && st == LBM_OK; ++k) {
-      st = enqueue_step(h, h->t, h->stream);
-      if (st == LBM_OK) h->t += 1;
-    }
+    st = enqueue_run(h, h->t, steps, h->stream);
+    if (st == LBM_OK) h->t += steps;
     if (st == LBM_OK && (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
                          cudaEventElapsedTime(&ms[c], e0, e1) != cudaSuccess))
       st = fail(h, LBM_ECUDA, "autotune timing: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1057,7 +1085,12 @@ lbm_status batch_build(lbm_batch* b, int parity) {
     cudaEventRecord(fork, b->root);
     for (size_t i = 0; i < b->h.size() && st == LBM_OK; ++i) {
       cudaStreamWaitEvent(b->branch[i], fork, 0);
-      for (int k = 0; k < kGraphSteps && st == LBM_OK; ++k) st = enqueue_step(b->h[i], parity + k, b->branch[i]);
+      if (st == LBM_OK) {
+        const long long before = b->h[i]->launches;  // captured: counted per replay
+        st = enqueue_run(b->h[i], parity, kGraphSteps, b->branch[i]);
+        b->h[i]->graph_kernels[parity] = b->h[i]->launches - before;
+        b->h[i]->launches = before;
+      }
       cudaEventRecord(joins[i], b->branch[i]);
       cudaStreamWaitEvent(b->root, joins[i], 0);
     }
@@ -1140,15 +1173,18 @@ lbm_status lbm_batch_step(lbm_batch* b, int n) {
     }
     for (; k + kGraphSteps <= n; k += kGraphSteps) {
       if (cudaGraphLaunch(b->graph[parity], b->stream) != cudaSuccess) return LBM_ECUDA;
-      for (lbm* h : b->h) h->t += kGraphSteps;
+      for (lbm* h : b->h) {
+        h->t += kGraphSteps;
+        h->launches += h->graph_kernels[parity];
+      }
     }
   }
   // the graph runs on the batch stream; later single steps of each handle go on that stream too
-  for (; k < n; ++k)
+  if (k < n)
     for (lbm* h : b->h) {
-      lbm_status st = enqueue_step(h, h->t, b->stream);
+      lbm_status st = enqueue_run(h, h->t, n - k, b->stream);
       if (st != LBM_OK) return st;
-      h->t += 1;
+      h->t += n - k;
     }
   // ... and each handle's stream then waits for the batch, so later per-handle calls stay in order
   if (cudaEventRecord(b->done, b->stream) != cudaSuccess) return LBM_ECUDA;

@@ -51,6 +51,11 @@ struct KernelSet {
   cudaError_t (*set_pop_c)(void* pop, const Geom& G, const Phys& P, int layout, int pdir, const double* in_r,
                            const double* in_b, double* acc_r, double* acc_b, cudaStream_t s);
   cudaError_t (*dens_from_acc)(const Geom& G, const double* acc_r, const double* acc_b, void* dens, cudaStream_t s);
+  // pass 1 preceded, on the plane z = nz-1, by the convective outflow of the step before (top: the
+  // outflow history), so that runs of steps launch the outflow kernel once at their end; null for
+  // compact storage
+  cudaError_t (*density_fold)(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag, void* top,
+                              int shape, cudaStream_t s);
 };
 
 const KernelSet* kernels_f64();

@@ -989,17 +989,87 @@ struct EmitLoop<27, Store, R, FAST, RECOL, FUSED, ODDT, BYv, TXv> {
 // ---------------------------------------------------------------------------
 // pass 1: density / phase field.  FIX: write the fixed-point accumulators of
 // the fused density pass instead (priming the fused pass from a stored state).
+// write one population pair at (node, dir) of a runtime direction (I/O kernels)
+template <class Store, typename R>
+__device__ __forceinline__ void store_pair(const Store& st, const KConst<R>& K, int64_t node, int dir, R fr, R fb) {
+  const R s = fr + fb;
+  const R q = s > R(0) ? fr / s : R(0.5);
+  st.store(node, dir, speed2_of(dir), K, fr, fb, s, q);
+}
+
+// the sum a warp_allsum over lanes 0..31 gives, with v[l] the value of lane l (the same
+// additions in the same order: at each stage lane l adds the value of lane l ^ o); v is consumed
+template <typename R>
+__device__ __forceinline__ R xor_tree_sum(R v[32]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int l = 0; l < o; ++l) v[l] = v[l] + v[l + o];
+  }
+  return v[0];
+}
+
+// The convective outflow of the step before (Sec. IV.A) for the column (x, y), by one thread:
+// the same arithmetic, in the same order, as k_outflow (which gives it to 27 lanes); `layout`
+// is the layout of the state the outflow completes.
+template <class Store, typename R>
+__device__ __forceinline__ void outflow_column(const Store& st, const Geom& G, const KConst<R>& K, int layout, int x,
+                                               int y, R* __restrict__ top) {
+  NodeMap below, here;
+  below.init(G, x, y, G.nz - 2);
+  here.init(G, x, y, G.nz - 1);
+  R fr[27], fb[27], a[32], m[32];
+#pragma unroll
+  for (int t = 0; t < 27; ++t) {
+    int64_t node;
+    int dir;
+    slot_of(below, layout, t, node, dir);
+    st.load_rb(node, dir, speed2_of(t), K, fr[t], fb[t]);
+    const R v = fr[t] + fb[t];
+    a[t] = v;
+    m[t] = cz_of(t) > 0 ? v : cz_of(t) < 0 ? -v : R(0);
+  }
+#pragma unroll
+  for (int t = 27; t < 32; ++t) a[t] = m[t] = R(0);
+  const R rho = xor_tree_sum(a);
+  const R mz = xor_tree_sum(m);
+  R F[3];
+  body_force(K, rho, F);
+  const R uz = (mz + R(0.5) * F[2]) / rho;
+  const R lam = uz > R(0) ? uz : R(0);
+  const R inv = R(1) / (R(1) + lam);
+  R* tr = top + ((int64_t)x + (int64_t)G.nx * y) * 64;
+#pragma unroll
+  for (int t = 0; t < 27; ++t) {
+    const R nr = (tr[t] + lam * fr[t]) * inv;
+    const R nb = (tr[32 + t] + lam * fb[t]) * inv;
+    tr[t] = nr;
+    tr[32 + t] = nb;
+    int64_t node;
+    int dir;
+    slot_of(here, layout, t, node, dir);
+    store_pair(st, K, node, dir, nr, nb);
+  }
+}
+
+// top != null (an outflow face): the threads of the plane z = nz-1 first complete the step
+// before with its convective outflow (outflow_column), so that k_outflow need not run between
+// the steps of a run; the blocks of the top planes start first (z blocks in reverse order).
+// Four blocks per SM (64 registers): the outflow path of the top plane may spill, the pass over
+// the rest of the box keeps its occupancy (a streaming pass, bound by memory parallelism).
 template <class Store, bool FIX, class B = BlkDefault>
-__global__ void __launch_bounds__(B::NT) k_density(Store st, Geom G,
+__global__ void __launch_bounds__(B::NT, 4) k_density(Store st, Geom G,
                                                       const __grid_constant__ KConst<typename DensOf<Store>::real> K,
                                                       int layout, typename DensOf<Store>::type* __restrict__ dens,
                                                       int* __restrict__ flag,
-                                                      unsigned long long* __restrict__ fix) {
+                                                      unsigned long long* __restrict__ fix,
+                                                      typename DensOf<Store>::real* __restrict__ top) {
   using D = typename DensOf<Store>::real;
   const int x = blockIdx.x * B::BX + threadIdx.x;
   const int y = blockIdx.y * B::BY + threadIdx.y;
-  const int z = blockIdx.z * B::BZ + threadIdx.z;
+  const int z = (gridDim.z - 1 - blockIdx.z) * B::BZ + threadIdx.z;
   if (x >= G.nx || y >= G.ny || z >= G.nz) return;
+  if (top != nullptr && z == G.nz - 1) outflow_column(st, G, K, layout, x, y, top);
   D rr = D(0), ft[27];
   if (fast_row(G, y, z)) {
     AoRow ar;
@@ -1688,13 +1758,6 @@ __global__ void __launch_bounds__(PTHREADS, MINB)
   EmitLoop2<0, Store>::run(st, K, base, m0, m1, odd != 0, f, rc);
 }
 
-// write one population pair at (node, dir) of a runtime direction (I/O kernels)
-template <class Store, typename R>
-__device__ __forceinline__ void store_pair(const Store& st, const KConst<R>& K, int64_t node, int dir, R fr, R fb) {
-  const R s = fr + fb;
-  const R q = s > R(0) ? fr / s : R(0.5);
-  st.store(node, dir, speed2_of(dir), K, fr, fb, s, q);
-}
 
 // sum over the 32 lanes of a warp, the same value in every lane (butterfly: lanes i and i^o
 // hold the same partial sum at every stage, as addition commutes exactly)

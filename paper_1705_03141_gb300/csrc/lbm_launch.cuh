@@ -53,25 +53,35 @@ struct Launch {
 
   template <class B>
   static cudaError_t density_b(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag, void* fix,
-                               cudaStream_t s) {
+                               void* top, cudaStream_t s) {
     if constexpr (fused) {
       if (fix) {
         k_density<Store, true, B><<<grid3<B>(G), dim3(B::BX, B::BY, B::BZ), 0, s>>>(
-            Tr::make(pop, G), G, kc(P), layout, static_cast<DT*>(dens), flag, static_cast<unsigned long long*>(fix));
+            Tr::make(pop, G), G, kc(P), layout, static_cast<DT*>(dens), flag, static_cast<unsigned long long*>(fix),
+            nullptr);
         return cudaGetLastError();
       }
     }
     k_density<Store, false, B><<<grid3<B>(G), dim3(B::BX, B::BY, B::BZ), 0, s>>>(
-        Tr::make(pop, G), G, kc(P), layout, static_cast<DT*>(dens), flag, nullptr);
+        Tr::make(pop, G), G, kc(P), layout, static_cast<DT*>(dens), flag, nullptr, static_cast<R*>(top));
     return cudaGetLastError();
+  }
+  static cudaError_t density_top(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag,
+                                 void* fix, void* top, int shape, cudaStream_t s) {
+    if constexpr (!std::is_same<R, double>::value) {  // FP64 keeps the default shape
+      if (shape == 1) return density_b<Blk<2, 4>>(pop, G, P, layout, dens, flag, fix, top, s);
+      if (shape == 2) return density_b<Blk<8, 1>>(pop, G, P, layout, dens, flag, fix, top, s);
+    }
+    return density_b<BlkDefault>(pop, G, P, layout, dens, flag, fix, top, s);
   }
   static cudaError_t density(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag, void* fix,
                              int shape, cudaStream_t s) {
-    if constexpr (!std::is_same<R, double>::value) {  // FP64 keeps the default shape
-      if (shape == 1) return density_b<Blk<2, 4>>(pop, G, P, layout, dens, flag, fix, s);
-      if (shape == 2) return density_b<Blk<8, 1>>(pop, G, P, layout, dens, flag, fix, s);
-    }
-    return density_b<BlkDefault>(pop, G, P, layout, dens, flag, fix, s);
+    return density_top(pop, G, P, layout, dens, flag, fix, nullptr, shape, s);
+  }
+  // pass 1 of a step that first completes the step before with its convective outflow
+  static cudaError_t density_fold(void* pop, const Geom& G, const Phys& P, int layout, void* dens, int* flag,
+                                  void* top, int shape, cudaStream_t s) {
+    return density_top(pop, G, P, layout, dens, flag, nullptr, top, shape, s);
   }
   // Tensor map of the pass-1 field for the TMA tile of k_collide_stream: 8-byte cells (rho, phi)
   // over (x, y, z + 1), planes z = -1 .. nz (dens points at plane 0, one plane above the start of
@@ -243,7 +253,7 @@ struct Launch {
         sizeof(DT),
         sizeof(R),
         &density, &collide, &outflow, &init, &get_pop, &set_pop, &top_from_state, &macro, Tr::paired, fused,
-        pipelined, false, nullptr, nullptr, nullptr, nullptr};
+        pipelined, false, nullptr, nullptr, nullptr, nullptr, &density_fold};
     return &ks;
   }
 };

@@ -26,7 +26,7 @@ Q = 27
 # every symbol include/lbm.h declares
 SYMBOLS = ["lbm_workspace_size", "lbm_create", "lbm_init_fields", "lbm_set_inflow", "lbm_step", "lbm_macro",
            "lbm_diag", "lbm_get_populations", "lbm_set_populations", "lbm_profile_step", "lbm_set_stream", "lbm_synchronize", "lbm_time",
-           "lbm_kernels_per_step", "lbm_last_error", "lbm_status_string", "lbm_moment_matrix", "lbm_selfcheck",
+           "lbm_kernels_per_step", "lbm_launch_count", "lbm_last_error", "lbm_status_string", "lbm_moment_matrix", "lbm_selfcheck",
            "lbm_diag_fields_static", "lbm_autotune", "lbm_batch_create", "lbm_batch_step", "lbm_batch_synchronize",
            "lbm_batch_free", "lbm_measure_fp32_peak", "lbm_selftest_tma", "lbm_kernel_variant", "lbm_kernel_block", "lbm_halo_bytes", "lbm_halo_pack",
            "lbm_halo_unpack", "lbm_step_pass", "lbm_free"]
@@ -84,6 +84,8 @@ def library():
         lib.lbm_time.argtypes = [h]
         lib.lbm_time.restype = ctypes.c_longlong
         lib.lbm_kernels_per_step.argtypes = [h]
+        lib.lbm_launch_count.argtypes = [h]
+        lib.lbm_launch_count.restype = ctypes.c_longlong
         lib.lbm_kernel_variant.argtypes = [h]
         lib.lbm_kernel_block.argtypes = [h]
         lib.lbm_last_error.argtypes = [h]
@@ -291,9 +293,14 @@ class Lattice:
         return library().lbm_kernels_per_step(self._h)
 
     @property
+    def launch_count(self):
+        """Kernel launches of this lattice's stepping so far (graph replays counted per kernel)."""
+        return library().lbm_launch_count(self._h)
+
+    @property
     def variant(self):
         """Collide-stream kernel in use: 1 one node per thread, 2 two nodes, 3 fused density pass,
-        4 software-pipelined."""
+        4 software-pipelined, 5 TMA-pipelined interior tiles."""
         return library().lbm_kernel_variant(self._h)
 
     @property

@@ -98,6 +98,7 @@ def test_null_handles(lib):
     lib.lbm_free(None)
     assert lib.lbm_time(None) == -1
     assert lib.lbm_kernel_variant(None) == -1
+    assert lib.lbm_launch_count(None) == -1
     assert lib.lbm_kernels_per_step(None) == -1
     assert lib.lbm_autotune(None, 4, None) == -1
     assert lib.lbm_batch_step(None, 1) == -1
