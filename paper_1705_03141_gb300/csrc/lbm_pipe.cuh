@@ -21,7 +21,8 @@
 //              4-byte cp.async tied to the stage's barrier; a lane on a reflecting x face reads
 //              plane T -/+ 2 of its own node instead (the mirror of AoRow);
 //   both       the (rho, phi) halo tile, 36 x TY x TZ cells as in k_collide_stream.
-// Every wait is bounded (mbar_wait): one that runs out raises kFlagTimeout, which
+// Every wait is bounded (mbar_wait_sleep: waiting warps sleep in the try-wait instead of spinning
+// on it, which leaves the issue slots to the other block of the SM): one that runs out raises kFlagTimeout, which
 // lbm_synchronize reports as LBM_ETIMEOUT, and the producer lets its issued copies land first.
 #pragma once
 #include "lbm_kernels.cuh"
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(TP_THREADS, TP_MINB)
     bool ok = true;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
       const int s = j % TP_S;
-      if (j >= TP_S && !mbar_wait(&empty[s], ((j / TP_S) & 1) ^ 1)) {
+      if (j >= TP_S && !mbar_wait_sleep(&empty[s], ((j / TP_S) & 1) ^ 1)) {
         ok = false;
         break;
       }
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(TP_THREADS, TP_MINB)
   int j = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
     const int s = j % TP_S;
-    bool ok = mbar_wait(&full[s], (j / TP_S) & 1);
+    bool ok = mbar_wait_sleep(&full[s], (j / TP_S) & 1);
     if (!ok) {
       if (lane == 0) atomicOr(flag, kFlagTimeout);
     }

@@ -52,6 +52,29 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long lon
     if (clock64() - t0 > cycles) return false;
   return true;
 }
+// mbar_try_wait with a suspend-time hint: a thread whose phase has not completed may sleep up to
+// `ns` nanoseconds inside the instruction instead of returning at once, so a waiting warp does not
+// spend issue slots spinning
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* b, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait as mbar_wait, sleeping between the polls
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* b, uint32_t parity, long long cycles = kWaitCycles,
+                                                uint32_t ns = 2000) {
+  if (mbar_try_wait_sleep(b, parity, ns)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait_sleep(b, parity, ns))
+    if (clock64() - t0 > cycles) return false;
+  return true;
+}
 // the barrier's current phase also waits for every cp.async this thread issued before (the
 // arrival count is unchanged: the pending count rises now and falls when those copies land)
 __device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* b) {
