@@ -1245,7 +1245,19 @@ __global__ void __launch_bounds__(B::NT, MINB)
   __shared__ uint64_t tbar;
 
   int x0 = blockIdx.x * B::BX, y0 = blockIdx.y * B::BY, z0 = blockIdx.z * B::BZ;
-  if (bmode) bt.boundary_tile(blockIdx.x, B::BY, B::BZ, x0, y0, z0);  // block 0: the tile at the origin
+  if (bmode) {
+    // the block's boundary tile, computed once (block 0: the tile at the origin)
+    __shared__ int3 btile;
+    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
+      int a, b, c;
+      bt.boundary_tile(blockIdx.x, B::BY, B::BZ, a, b, c);
+      btile = make_int3(a, b, c);
+    }
+    __syncthreads();
+    x0 = btile.x;
+    y0 = btile.y;
+    z0 = btile.z;
+  }
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
   const bool active = x < G.nx && y < G.ny && z < G.nz;
   const int tid = threadIdx.x + B::BX * (threadIdx.y + B::BY * threadIdx.z);
