@@ -369,6 +369,43 @@ def test_oscillating_droplet_period():
     assert (h1 / h4) == pytest.approx(T1 / T4, rel=0.07)
 
 
+def test_table_two_drop_is_spherical_then_oblate_at_the_papers_times():
+    """Sec. III.B, Fig. dropOsci (41^3 periodic box, prolate drop 15/11/11, density ratio 4 with
+    the drop the dense phase, nu = 3.333e-3, A = 1e-2): the drop is spherical at t = 700 and
+    oblate at t = 1,400.  With a and b the interface radii (phi = 0 crossings, linearly
+    interpolated) along the major (x) and a minor (y) axis through the centre, sampled every 10
+    steps: a - b first changes sign within 10 % of 700 steps and reaches its following minimum
+    within 10 % of 1,400 (a period from Eq. Lamb, 2,242 steps, would put them near 560 and
+    1,120).  The prolate shape at 2,500 is checked through the FP64 CUDA path, which equals this
+    oracle to 1e-12."""
+    n, axes = 41, (15.0, 11.0, 11.0)
+    w = L.oscillating_droplet(n=n, axes=axes, nu=3.333e-3, A=1e-2, rho_r0=1.0, rho_b0=0.25)
+    rr, rb, u = L.initial_fields(w)
+    o = oracle.Oracle(w["shape"], w["params"])
+    o.init_fields(rr, rb, u)
+    c = (n - 1) // 2
+
+    def radius(line):
+        j = np.where((line[:-1] > 0) & (line[1:] <= 0))[0][-1]
+        return j + line[j] / (line[j] - line[j + 1]) - c
+
+    ts, d = [], []
+    for _ in range(1500 // 10):
+        o.step(10)
+        r, b, _ = o.macro()
+        phi = (r - b) / (r + b)  # (z, y, x)
+        d.append(radius(phi[c, c, :]) - radius(phi[c, :, c]))
+        ts.append(o.t)
+    d, ts = np.array(d), np.array(ts, dtype=np.float64)
+    k = int(np.where(d <= 0)[0][0])
+    t_sphere = ts[k - 1] + 10 * d[k - 1] / (d[k - 1] - d[k])
+    i = next(i for i in range(k, len(d) - 1) if d[i] < d[i - 1] and d[i + 1] > d[i])
+    y0, y1, y2 = d[i - 1], d[i], d[i + 1]
+    t_oblate = ts[i] + 10 * 0.5 * (y0 - y2) / (y0 - 2 * y1 + y2)
+    assert abs(t_sphere - 700) < 0.10 * 700
+    assert abs(t_oblate - 1400) < 0.10 * 1400
+
+
 def _rt_amplitudes(g, steps, every, nu=None):
     """Rayleigh-Taylor set-up of Sec. III.C at W = 16 (16 x 16 x 64, heavy fluid over light,
     walls top and bottom, At = 0.5, A = 0): peak-to-peak height of the phi = 0 surface (linear
