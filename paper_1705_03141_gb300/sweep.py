@@ -9,6 +9,9 @@ the batch throughput (CUDA events around the graph launches only) and writes
 the trajectories, which are the training data of the surrogate.
 
     python -m paper_1705_03141_gb300.sweep [--n 64] [--steps 20000] [--samples 64] [--out sweep.json]
+
+With --paper-cases the batch holds the three jets of Sec. IV.C (Table IV: the reference jet, Case 1
+and Case 2, `lbm_inputs.paper_jet_cases`) instead of the random sweep.
 """
 from __future__ import annotations
 
@@ -78,11 +81,14 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=2024)
     ap.add_argument("--storage", default="f16")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--paper-cases", action="store_true", help="the three jets of Table IV instead of the sweep")
     args = ap.parse_args(argv)
+    works = list(L.paper_jet_cases().values()) if args.paper_cases else None
     import torch
 
     torch.cuda.set_device(0)
-    res = run_sweep(n=args.n, steps=args.steps, samples=args.samples, seed=args.seed, storage=args.storage)
+    res = run_sweep(n=args.n, steps=args.steps, samples=args.samples, seed=args.seed, storage=args.storage,
+                    works=works)
     txt = json.dumps(res)
     if args.out:
         with open(args.out, "w") as f:

@@ -1,0 +1,128 @@
+"""Numbers the paper prints, read from `tests/golden/`, against the relations and set-ups built here.
+
+Each fixture keeps the paper's numbers as printed; a value is matched to half a unit in its last
+printed digit.  Pinned here: Eq. (sigma) with tau = 3 nu + 1/2 (the sigma column of Table II), the
+lattice mapping of the jets (the lattice values of Sec. IV.A from the groups of Table III) and the
+breakup-regime labels of the batched sweep (the regimes Sec. IV.C expects for the jets of Table IV).
+"""
+import json
+import math
+import os
+
+import pytest
+
+import lbm_inputs as L
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+ROMAN = {"0": 0, "I": 1, "II": 2, "III": 3}
+
+
+def _load(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def printed(s):
+    """(value, half a unit in the last printed digit) of a number as the paper prints it."""
+    mant, _, exp = s.lower().partition("e")
+    decimals = len(mant.split(".")[1]) if "." in mant else 0
+    return float(s), 0.5 * 10.0 ** (int(exp or 0) - decimals)
+
+
+def matches(x, s):
+    v, half = printed(s)
+    return abs(x - v) <= half * (1 + 1e-9)
+
+
+def test_printed_precision_helper():
+    assert printed("2.27e-3") == (2.27e-3, pytest.approx(5e-6))
+    assert printed("0.70") == (0.70, pytest.approx(5e-3))
+    assert printed("3.4e3") == (3.4e3, pytest.approx(50.0))
+    assert printed("25") == (25.0, 0.5)
+    assert matches(1.4286, "1.4") and not matches(1.46, "1.4")
+
+
+def sigma_eq(A, nu):
+    """Eq. (sigma) with tau = 3 nu + 1/2, the relaxation time of the viscous moments."""
+    return 4.0 / 9.0 * A * (3.0 * nu + 0.5)
+
+
+def test_eq_sigma_reproduces_the_sigma_column_of_table_two():
+    """Table II prints sigma beside nu and A for all six oscillating-drop runs.  Eq. (sigma) with
+    tau = 3 nu + 1/2 gives every entry to its three printed digits; the readings of tau it excludes
+    (tau = 3 nu, a fixed tau = 1, sigma proportional to 1/tau) each miss the column."""
+    rows = _load("table_two_oscillating_drop.json")["rows"]
+    assert len(rows) == 6
+    for nu_s, A_s, sig_s, _ in rows:
+        nu, A = float(nu_s), float(A_s)
+        assert matches(sigma_eq(A, nu), sig_s), (nu_s, A_s, sig_s, sigma_eq(A, nu))
+    wrong = (lambda A, nu: 4.0 / 9.0 * A * 3.0 * nu,
+             lambda A, nu: 4.0 / 9.0 * A,
+             lambda A, nu: 4.0 / 9.0 * A / (3.0 * nu + 0.5),
+             lambda A, nu: 2.0 / 9.0 * A * (3.0 * nu + 0.5))
+    for f in wrong:
+        assert not all(matches(f(float(r[1]), float(r[0])), r[2]) for r in rows)
+
+
+def test_jet_mapping_gives_the_lattice_values_of_section_four_a():
+    """Sec. IV.A derives the jet's lattice values from the groups of Table III with D = 25,
+    rho_j = 1, u_j0 = 0.1 (Eqs. densityRatio-Froude).  The mapping of the sweep and the surrogate
+    (jet_from_groups), fed those groups, gives each printed lattice value to its printed digits:
+    nu_j = u D / Re, nu_c = nu_j / eta, sigma = rho_j u^2 D / We, g = u^2 / (Fr D), and the box
+    8D x 8D x 20D.  A slip in the mapping (nu_c = eta nu_j, g = u^2 Fr / D, sigma from We without
+    the square of u) misses these digits by far."""
+    j = _load("jet_lattice_units.json")
+    w = L.paper_jet_cases()["ref"]
+    p, g = w["params"], w["groups"]
+    D = printed(j["D"])[0]
+    assert w["shape"] == tuple(int(printed(k)[0] * D) for k in j["box_in_D"])
+    assert matches(g["D"], j["D"]) and matches(g["u_j0"], j["u_j0"]) and matches(p["rho_r0"], j["rho_j"])
+    lat = j["lattice"]
+    assert matches(p["nu_r"], lat["nu_j"])
+    assert matches(p["nu_b"], lat["nu_c"])
+    assert matches(p["rho_b0"], lat["rho_c"])
+    assert matches(p["g"][2], lat["g"]) and p["g"][:2] == (0.0, 0.0)
+    sigma = p["rho_r0"] * g["u_j0"] ** 2 * g["D"] / g["We"]  # Eq. jetWeber
+    assert matches(sigma, lat["sigma"])
+    grp = j["groups"]
+    assert matches(g["Re"], grp["Re"]) and matches(g["We"], grp["We"]) and matches(g["eta"], grp["eta"])
+    assert matches(g["u_j0"] ** 2 / (p["g"][2] * g["D"]), grp["Fr"])
+    assert matches(p["rho_r0"] / p["rho_b0"], grp["gamma"])
+    # the printed gamma = 1.4 taken exactly would put rho_c at 0.714, off the printed 0.70
+    assert not matches(1.0 / printed(grp["gamma"])[0], lat["rho_c"])
+
+
+def test_table_four_groups_and_the_case_two_reading():
+    """We = (Re Oh)^2 (Sec. IV.C) holds to the printed digits for the reference jet and Case 1.
+    For Case 2 the printed Oh = 3.0e-3 gives We = 1.0e2, not the printed 1.0e4; Oh = 3.0e-2 gives
+    1.0e4, and it is the value the workload uses."""
+    cases = {c["name"]: c for c in _load("table_four_regimes.json")["cases"]}
+    for name in ("ref", "case1"):
+        c = cases[name]
+        assert matches((float(c["Re"]) * float(c["Oh"])) ** 2, c["We"])
+    c2 = cases["case2"]
+    assert not matches((float(c2["Re"]) * float(c2["Oh"])) ** 2, c2["We"])
+    assert matches((float(c2["Re"]) * 3.0e-2) ** 2, c2["We"])
+    w = L.paper_jet_cases()["case2"]["groups"]
+    assert math.isclose(w["Oh"], 3.0e-2, rel_tol=1e-12) and matches(w["We"], c2["We"])
+
+
+def test_table_four_jets_fall_in_the_regimes_the_paper_expects():
+    """Sec. IV.C expects sinuous breakup (II) for the reference jet, dripping or varicose (0 or I)
+    for Case 1 and atomization (III) for Case 2.  The sweep's labels (Oh = 2.8/Re and 22/Re, We < 4
+    dripping) put the workloads of those jets there, with the groups they reach on the lattice (no
+    cap of the mapping binds: the reached groups are the targets)."""
+    cases = _load("table_four_regimes.json")["cases"]
+    works = L.paper_jet_cases()
+    for c in cases:
+        w = works[c["name"]]
+        g = w["groups"]
+        assert matches(g["Re"], c["Re"]) and matches(g["We"], c["We"])
+        assert math.isclose(g["Oh"], g["Oh_target"], rel_tol=1e-12)
+        assert g["regime"] == L.regime_label(g["Re"], g["Oh"], g["We"])
+        assert g["regime"] in [ROMAN[r] for r in c["regimes"]], (c["name"], g["regime"])
+        assert w["shape"] == (200, 200, 500)
+        assert g["u_j0"] <= 0.1 and w["params"]["A"] < 0.02
+    # Case 1 reaches its Re as the paper does: a larger jet viscosity and a slower jet
+    assert works["case1"]["params"]["nu_r"] > works["ref"]["params"]["nu_r"]
+    assert works["case1"]["groups"]["u_j0"] < works["ref"]["groups"]["u_j0"]

@@ -10,6 +10,9 @@ sqrt(g) scaling of the Rayleigh-Taylor growth rate (linear theory), and a
 passive colour front carried through the nozzle inlet and the convective
 outflow.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -378,8 +381,13 @@ def test_table_two_drop_is_spherical_then_oblate_at_the_papers_times():
     within 10 % of 1,400 (a period from Eq. Lamb, 2,242 steps, would put them near 560 and
     1,120).  The prolate shape at 2,500 is checked through the FP64 CUDA path, which equals this
     oracle to 1e-12."""
-    n, axes = 41, (15.0, 11.0, 11.0)
-    w = L.oscillating_droplet(n=n, axes=axes, nu=3.333e-3, A=1e-2, rho_r0=1.0, rho_b0=0.25)
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table_two_oscillating_drop.json")) as f:
+        table = json.load(f)  # the paper's printed set-up, first row of Table II and snapshot times
+    n, axes = int(table["setup"]["box"]), tuple(float(a) for a in table["setup"]["axes"])
+    nu, A = (float(v) for v in table["rows"][0][:2])
+    t_sph, t_obl = float(table["snapshots"]["spherical"]), float(table["snapshots"]["oblate"])
+    assert float(table["setup"]["density_ratio"]) == 4.0  # read as rho_r0 = 1 (the drop), rho_b0 = 0.25
+    w = L.oscillating_droplet(n=n, axes=axes, nu=nu, A=A, rho_r0=1.0, rho_b0=0.25)
     rr, rb, u = L.initial_fields(w)
     o = oracle.Oracle(w["shape"], w["params"])
     o.init_fields(rr, rb, u)
@@ -402,8 +410,8 @@ def test_table_two_drop_is_spherical_then_oblate_at_the_papers_times():
     i = next(i for i in range(k, len(d) - 1) if d[i] < d[i - 1] and d[i + 1] > d[i])
     y0, y1, y2 = d[i - 1], d[i], d[i + 1]
     t_oblate = ts[i] + 10 * 0.5 * (y0 - y2) / (y0 - 2 * y1 + y2)
-    assert abs(t_sphere - 700) < 0.10 * 700
-    assert abs(t_oblate - 1400) < 0.10 * 1400
+    assert abs(t_sphere - t_sph) < 0.10 * t_sph
+    assert abs(t_oblate - t_obl) < 0.10 * t_obl
 
 
 def _rt_amplitudes(g, steps, every, nu=None):
