@@ -252,10 +252,10 @@ PAPER_JETS = (("ref", 3.4e3, 4.4e-3, 0.1), ("case1", 4.6e2, 4.4e-3, 0.025), ("ca
 
 
 def paper_jet_cases(t_star=20.0, noise=0.01, seed=0):
-    """The three jets of Sec. IV.C on the lattice of Sec. IV.A: nozzle D = 25 in an 8D x 8D x 20D box
+    """The three jets of Sec. IV.C on the lattice of Sec. IV.B: nozzle D = 25 in an 8D x 8D x 20D box
     (200 x 200 x 500), rho_j = 1, rho_c = 0.70, viscosity ratio 4.2, Fr = 8.5, each run to t = t* D/u_j0.
 
-    * ref: Re = 3.4e3, Oh = 4.4e-3 (We = 2.2e2) at u_j0 = 0.1, the jet of Sec. IV.A; the mapping of
+    * ref: Re = 3.4e3, Oh = 4.4e-3 (We = 2.2e2) at u_j0 = 0.1, the jet of Sec. IV.B; the mapping of
       jet_from_groups then gives that section's lattice values (nu_j = 7.4e-4, nu_c = 1.8e-4,
       sigma = 1.1e-3, g = 4.7e-5).
     * case1: Re = 4.6e2 at the same Oh (We = 4.1).  As in the paper, Re is lowered by a larger jet
@@ -263,7 +263,7 @@ def paper_jet_cases(t_star=20.0, noise=0.01, seed=0):
     * case2: Re = 3.4e3, Oh = 3.0e-2 (We = 1.0e4).  Table IV prints Oh = 3.0e-3 beside We = 1.0e4; both
       We = (Re Oh)^2 and the text (Oh raised by a lower sigma, the case in Regime III) need 3.0e-2.
 
-    Sec. IV.A prints rho_c = 0.70 beside gamma = 1.4: the lattice value is kept (gamma = 1/0.70 = 1.43,
+    Sec. IV.B prints rho_c = 0.70 beside gamma = 1.4: the lattice value is kept (gamma = 1/0.70 = 1.43,
     which the two printed digits round to 1.4).  No cap of jet_from_groups binds, so the recorded groups
     are the targets."""
     D = 25.0

@@ -15,9 +15,11 @@ than itself (App. A/B identities, conservation laws, the BGK limit, the
 shear-wave decay rate of Eq. (shear), uniform-force momentum gain, the
 Laplace law with Eq. (sigma), linear Rayleigh-Taylor growth, and a passive
 colour front carried through the nozzle inlet and the convective outflow).
-Parity unpinned: the Rayleigh-Taylor and jet set-ups have no printed numbers
-to compare with (figures only); they are covered by the conservation,
-boundary and growth-rate pins instead.
+The diagnostics (colour masses, the Laplace pressure jump, the jet's leading
+edge) are pinned on constructed fields with closed-form answers.  Parity
+unpinned: the jet set-up has no printed numbers to compare with (figures
+only), and the Rayleigh-Taylor fronts only their dependence on Re; they are
+covered by the conservation, boundary and growth-rate pins instead.
 """
 from __future__ import annotations
 
@@ -205,6 +207,40 @@ def equilibrium(rho_k, u, alpha, Phi_vec=None):
 
 def alpha_r(params: dict) -> float:
     return lib().orc_alpha_r(ctypes.byref(make_params(params)))
+
+
+def diagnostics(rho_r, rho_b, params: dict) -> dict:
+    """FP64 diagnostics of density fields of shape (nz, ny, nx), as the paper measures them.
+
+    mass_r, mass_b: the total of each colour.
+    dp: the Laplace pressure jump of Sec. III.A, measured "as Leclaire 2012" (Eq. lap): the pressure of
+        Eq. (press), p = sum_k rho_k 9(1 - alpha_k)/19, averaged over the nodes with phi > 0.99 minus
+        its average over the nodes with phi < -0.99; 0 when either set is empty.
+    z_le: the jet's leading-edge position of Sec. IV.B (Fig. penetration): the highest plane z that
+        holds a node with phi > 0; on that plane every such node is refined to the phi = 0 crossing
+        toward z + 1 by linear interpolation, and the largest value is the position (z itself when
+        the plane is the top one); -1 when no node has phi > 0.
+    phi = (rho_r - rho_b)/(rho_r + rho_b) throughout.
+    """
+    r = np.asarray(rho_r, dtype=np.float64)
+    b = np.asarray(rho_b, dtype=np.float64)
+    phi = (r - b) / (r + b)
+    ar, ab = alpha_r(params), 8.0 / 27.0
+    p = r * (9.0 * (1.0 - ar) / 19.0) + b * (9.0 * (1.0 - ab) / 19.0)
+    inside, outside = phi > 0.99, phi < -0.99
+    dp = float(p[inside].mean() - p[outside].mean()) if inside.any() and outside.any() else 0.0
+    red_planes = np.nonzero((phi > 0.0).any(axis=(1, 2)))[0]
+    if red_planes.size == 0:
+        z_le = -1.0
+    else:
+        z = int(red_planes[-1])
+        if z == phi.shape[0] - 1:
+            z_le = float(z)
+        else:
+            here, above = phi[z], phi[z + 1]
+            red = here > 0.0
+            z_le = float(np.max(z + here[red] / (here[red] - above[red])))
+    return {"mass_r": float(r.sum()), "mass_b": float(b.sum()), "z_le": z_le, "dp": dp}
 
 
 def noise(seed, t, node, comp) -> float:

@@ -2,7 +2,7 @@
 
 Each fixture keeps the paper's numbers as printed; a value is matched to half a unit in its last
 printed digit.  Pinned here: Eq. (sigma) with tau = 3 nu + 1/2 (the sigma column of Table II), the
-lattice mapping of the jets (the lattice values of Sec. IV.A from the groups of Table III) and the
+lattice mapping of the jets (the lattice values of Sec. IV.B from the groups of Table III) and the
 breakup-regime labels of the batched sweep (the regimes Sec. IV.C expects for the jets of Table IV).
 """
 import json
@@ -64,8 +64,8 @@ def test_eq_sigma_reproduces_the_sigma_column_of_table_two():
         assert not all(matches(f(float(r[1]), float(r[0])), r[2]) for r in rows)
 
 
-def test_jet_mapping_gives_the_lattice_values_of_section_four_a():
-    """Sec. IV.A derives the jet's lattice values from the groups of Table III with D = 25,
+def test_jet_mapping_gives_the_lattice_values_of_section_four_b():
+    """Sec. IV.B derives the jet's lattice values from the groups of Table III with D = 25,
     rho_j = 1, u_j0 = 0.1 (Eqs. densityRatio-Froude).  The mapping of the sweep and the surrogate
     (jet_from_groups), fed those groups, gives each printed lattice value to its printed digits:
     nu_j = u D / Re, nu_c = nu_j / eta, sigma = rho_j u^2 D / We, g = u^2 / (Fr D), and the box
