@@ -16,10 +16,11 @@ shear-wave decay rate of Eq. (shear), uniform-force momentum gain, the
 Laplace law with Eq. (sigma), linear Rayleigh-Taylor growth, and a passive
 colour front carried through the nozzle inlet and the convective outflow).
 The diagnostics (colour masses, the Laplace pressure jump, the jet's leading
-edge) are pinned on constructed fields with closed-form answers.  Parity
-unpinned: the jet set-up has no printed numbers to compare with (figures
-only), and the Rayleigh-Taylor fronts only their dependence on Re; they are
-covered by the conservation, boundary and growth-rate pins instead.
+edge) are pinned on constructed fields with closed-form answers, the jet's
+head speed on the momentum balance at its stagnation point.  Parity unpinned:
+the jet's leading-edge history itself (a figure, no printed numbers), and the
+Rayleigh-Taylor fronts beyond their dependence on Re; they are covered by the
+conservation, boundary and growth-rate pins instead.
 """
 from __future__ import annotations
 

@@ -6,9 +6,10 @@ balance, the BGK limit (an independent numpy transcription), the viscosity of
 Eq. (shear) from shear-wave decay, the sound speed of Eq. (press), steady
 Poiseuille flow between halfway bounce-back walls, Laplace's law with
 Eq. (sigma), the Lamb / Miller-Scriven oscillation period, the sign and
-sqrt(g) scaling of the Rayleigh-Taylor growth rate (linear theory), and a
+sqrt(g) scaling of the Rayleigh-Taylor growth rate (linear theory), a
 passive colour front carried through the nozzle inlet and the convective
-outflow.
+outflow, and the head speed of a jet against the momentum balance at its
+stagnation point.
 """
 import json
 import os
@@ -443,6 +444,46 @@ def _rt_amplitudes(g, steps, every, nu=None):
         r, b, _ = o.macro()
         amp.append(height(r, b))
     return np.array(amp)
+
+
+def _jet_head_speed(gamma, steps=800, every=25, window=(300, 800)):
+    """Leading-edge speed (Sec. IV.B, oracle.diagnostics) of a jet of red fluid (rho_j = 1, nozzle
+    D = 6, u_j0 = 0.1, Re = 200, equal viscosities, A = 1e-3, no gravity, no inlet noise) entering
+    blue fluid of density 1/gamma at rest in a 24 x 24 x 72 box: least-squares slope of z_le(t)
+    over the window of steps."""
+    w = L.jet(nx=24, ny=24, nz=72, D=6.0, Re=200.0, nu_c=0.003, gamma=gamma, eta=1.0, A=1e-3, noise=0.0)
+    p = {**w["params"], "g": (0.0, 0.0, 0.0)}
+    rr, rb, u = L.initial_fields(w)
+    o = oracle.Oracle(w["shape"], p)
+    o.init_fields(rr, rb, u)
+    ts, zs = [], []
+    for _ in range(steps // every):
+        o.step(every)
+        r, b, _ = o.macro()
+        ts.append(o.t)
+        zs.append(oracle.diagnostics(r, b, p)["z_le"])
+    ts, zs = np.array(ts, dtype=np.float64), np.array(zs)
+    sel = (ts >= window[0]) & (ts <= window[1])
+    assert zs[sel].max() < 72 - 12, "the head reached the outflow plane"
+    return np.polyfit(ts[sel], zs[sel], 1)[0], p["inflow"]["u_j0"]
+
+
+@pytest.mark.slow
+def test_jet_head_speed_follows_the_momentum_balance_at_the_head():
+    """The whole jet path (nozzle inlet, interface, ambient displaced through the convective
+    outflow) against the momentum balance at the head of a jet entering a fluid at rest: in the
+    head's frame the jet's and the ambient's stagnation pressures are equal,
+    rho_j (u_j - u_h)^2 = rho_c u_h^2, so u_h = u_j / (1 + (rho_c/rho_j)^(1/2)) (the penetration
+    speed of Birkhoff, MacDougall, Pugh and Taylor 1948).  Viscosity and the starting vortex slow
+    both heads alike (measured 0.375 and 0.508 u_j, 75 % of the inviscid 0.5 and 0.667), so the
+    ratio of head speeds at density ratios gamma = 4 and 1 is held to the formula's 4/3 within 4 %
+    (measured 1.354 over steps 300-800, t* = 5-13).  An inertia that ignored the density ratio
+    gives 1.0; momentum mixing linear in the densities, rho_j/(rho_j + rho_c), gives 1.6."""
+    u1, uj = _jet_head_speed(1.0)
+    u4, _ = _jet_head_speed(4.0)
+    assert u4 / u1 == pytest.approx(4.0 / 3.0, rel=0.04)
+    for u, inviscid in ((u1, 0.5 * uj), (u4, uj / 1.5)):
+        assert 0.6 * inviscid < u < inviscid
 
 
 def test_rayleigh_taylor_sign_of_buoyancy():
