@@ -3,8 +3,9 @@ against the oracle's definitions of them, evaluated on the same density fields (
 returns), after steps of the CUDA path on boxes with a drop, blobs crossing every face, and a jet.
 
 The device reduces in a fixed order, the oracle in numpy's; the per-node arithmetic is the same
-definition.  Masses and the pressure means agree to rounding (1e-12 relative), the leading edge
-to 1e-12 lattice units.
+definition.  Masses agree to rounding (1e-11 relative: sums of up to 33k positive terms in two
+orders), the pressure jump to 1e-12 of the largest density, the leading edge (the same division
+on the same values) to 1e-12 lattice units.
 """
 import numpy as np
 import pytest
@@ -31,8 +32,8 @@ def test_diag_equals_the_oracle_definitions(cuda, name, storage):
     lat.close()
     o = oracle.diagnostics(r, b, work["params"])
     assert np.isfinite(r).all() and np.isfinite(b).all()
-    assert d["mass_r"] == pytest.approx(o["mass_r"], rel=1e-12)
-    assert d["mass_b"] == pytest.approx(o["mass_b"], rel=1e-12)
+    assert d["mass_r"] == pytest.approx(o["mass_r"], rel=1e-11)
+    assert d["mass_b"] == pytest.approx(o["mass_b"], rel=1e-11)
     assert d["z_le"] == pytest.approx(o["z_le"], abs=1e-12)
     scale = max(float(np.max(r)), float(np.max(b)))
     assert d["dp"] == pytest.approx(o["dp"], abs=1e-12 * scale)
