@@ -56,7 +56,7 @@ class OrcParams(ctypes.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle (gcc -O2 -fopenmp) into oracle/_build/."""
+    """Compile the oracle (gcc -O3 -fopenmp) into oracle/_build/."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
