@@ -52,6 +52,7 @@ class OrcParams(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("perturb_literal", ctypes.c_int),
         ("ghost_mode", ctypes.c_int),
+        ("drop_Phi", ctypes.c_int),
     ]
 
 
@@ -120,6 +121,7 @@ def make_params(p: dict) -> OrcParams:
     o.seed = p.get("seed", 0)
     o.perturb_literal = int(p.get("perturb_literal", 0))
     o.ghost_mode = int(p.get("ghost_mode", 0))
+    o.drop_Phi = int(p.get("drop_Phi", 0))
     return o
 
 

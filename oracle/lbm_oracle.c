@@ -19,6 +19,8 @@
  *   R1  Eq. (perturb) is taken with the square restored: w_i (c_i.grad phi)^2/|grad phi|^2.
  *       The printed, unsquared form is kept behind `perturb_literal` so the
  *       tests can show that it breaks per-colour mass conservation.
+ *       (Likewise `drop_Phi` removes the Phi term of Eq. (EES), so the tests
+ *       can show what it does for a translating drop.)
  *   R3  the body force |F> enters once per node, split between the colours
  *       as (rho_k/rho)|F>.
  *   R5  cos(theta_1) = 0 for the rest vector.
@@ -171,6 +173,7 @@ typedef struct {
   int perturb_literal;     /* 1: Eq. (perturb) exactly as printed (no square) */
   int ghost_mode;          /* gradient ghost next to a wall: 0 mirror (R10); 1 periodic wrap and
                               2 mirror about the wall node are planted mistakes for the tests */
+  int drop_Phi;            /* 1: Phi_i^k = 0 in the collision (a planted mistake for the tests) */
 } orc_params;
 
 /* alpha_b = 8/27 (Sec. II); Grunau relation gamma = (1-alpha_b)/(1-alpha_r). */
@@ -405,6 +408,7 @@ static void node_update(const orc_params* p, const dims* d, const double* f, con
     const double* gk = k == 0 ? grr : grb;
     double Phi[Q], feq[Q], neq[Q], m[Q], coll[Q];
     orc_Phi(nubar, u, gk, Phi);
+    if (p->drop_Phi) memset(Phi, 0, sizeof Phi);
     equilibrium(rho_k, u, alpha_k, Phi, feq);
     for (int i = 0; i < Q; ++i) neq[i] = fk[i] - feq[i];
     matvec(MM, 1.0, neq, m);
