@@ -446,6 +446,46 @@ def _rt_amplitudes(g, steps, every, nu=None):
     return np.array(amp)
 
 
+def _shear_layers(rates, steps=600, every=50, nu=1e-4, U=0.1):
+    """Largest |u| every `every` steps (NaN once the run diverged) of two periodic shear layers,
+    u_x = U [tanh(z - nz/4) - tanh(z - 3nz/4) - 1] with a 5 % sinusoidal u_z kick, in a 32 x 4 x 32
+    periodic box; red fills the band between the layers and blue the rest (tanh interfaces of width
+    4 on the layers), density ratio 1, A = 1e-3, nu = 1e-4 for both colours."""
+    w = L.static_droplet(n=32, R=4.0, nu_r=nu, nu_b=nu, A=1e-3)
+    p = dict(w["params"])
+    if rates is not None:
+        p["s"] = rates
+    nx, ny, nz = 32, 4, 32
+    z, _, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(ny, dtype=np.float64),
+                          np.arange(nx, dtype=np.float64), indexing="ij")
+    ux = U * (np.tanh(z - nz / 4) - np.tanh(z - 3 * nz / 4) - 1.0)
+    u = np.stack([ux, np.zeros_like(ux), 0.05 * U * np.sin(2 * np.pi * x / nx)])
+    red = 0.25 * (1 + np.tanh((z - nz / 4) / 2.0)) * (1 - np.tanh((z - 3 * nz / 4) / 2.0))
+    o = oracle.Oracle((nx, ny, nz), p)
+    o.init_fields(red, 1.0 - red, u)
+    out = []
+    for _ in range(steps // every):
+        o.step(every)
+        v = o.macro()[2]
+        out.append(float(np.abs(v).max()) if np.isfinite(v).all() else float("nan"))
+        if not np.isfinite(out[-1]):
+            break
+    return out
+
+
+def test_suga_rates_keep_a_low_viscosity_shear_layer_stable_where_bgk_diverges():
+    """Sec. II: with Suga's relaxation rates the MRT operator stays stable at kinematic viscosities
+    of order 1e-4, where a single-relaxation-time (BGK) collision does not.  Two thin shear layers
+    (velocity jump 0.2 over about two nodes, nu = 1e-4, Re per node ~ 1,000) carrying the
+    interfaces: with the default rates the largest velocity stays below 0.2 for 600 steps
+    (measured 0.135); with every rate equal to 1/tau (BGK limit, same viscosity) the run diverges
+    before step 600 (non-finite by step 450)."""
+    mrt = _shear_layers(None)
+    assert len(mrt) == 12 and all(np.isfinite(mrt)) and max(mrt) < 0.2
+    bgk = _shear_layers(L.uniform_rates(1.0 / (3.0 * 1e-4 + 0.5)))
+    assert not np.isfinite(bgk[-1])
+
+
 def _drop_after_one_crossing(U, **over):
     """phi and u of a drop (24^3 periodic, R = 6, density ratio 4, nu = 0.01, A = 1e-3) after the
     steps in which a velocity of 0.05 carries it once across the box, started at rest (U = 0) or
