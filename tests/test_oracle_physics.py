@@ -521,6 +521,33 @@ def test_suga_rates_keep_a_low_viscosity_shear_layer_stable_where_bgk_diverges()
     assert not np.isfinite(bgk[-1])
 
 
+@pytest.mark.slow
+def test_jet_grows_a_mushroom_head_by_t_star_3():
+    """Sec. IV.B: the jet of Table III (Re = 3.4e3, We = 2.2e2, density ratio 1/0.70, viscosity
+    ratio 4.2, lattice mapping of Sec. IV.B) has formed a mushroom-like head at t* = t u_j0/D = 3.
+    Here at D = 8 in a 40 x 40 x 64 box, no inlet noise: at t* = 3 the widest red cross-section of
+    the head (the upper half of the red column) is at least 1.25 times the stem's just above the
+    nozzle, z in [D/2, 3D/4] (measured 1.41: largest red node radius 6.7 against 4.7), with the
+    leading edge between 1.5 D and 2.5 D (1.74 D)."""
+    D, u = 8.0, 0.1
+    w = L.jet_from_groups(3.4e3, np.sqrt(2.2e2) / 3.4e3, 1.0 / 0.70, 4.2, D=D, nxy=40, nz=64, u_max=u, noise=0.0)
+    rr, rb, v = L.initial_fields(w)
+    o = oracle.Oracle(w["shape"], w["params"])
+    o.init_fields(rr, rb, v)
+    o.step(int(round(3.0 * D / u)))
+    r, b, _ = o.macro()
+    phi = (r - b) / (r + b)
+    nz, ny, nx = phi.shape
+    yy, xx = np.meshgrid(np.arange(ny) - 0.5 * (ny - 1), np.arange(nx) - 0.5 * (nx - 1), indexing="ij")
+    rad = np.hypot(xx, yy)
+    width = np.array([rad[phi[z] > 0].max() if (phi[z] > 0).any() else 0.0 for z in range(nz)])
+    top = oracle.diagnostics(r, b, w["params"])["z_le"]
+    stem = width[int(D / 2):int(3 * D / 4) + 1].max()
+    head = width[int(top / 2):int(top) + 1].max()
+    assert 1.5 * D < top < 2.5 * D
+    assert head > 1.25 * stem, (head, stem)
+
+
 def _drop_after_one_crossing(U, **over):
     """phi and u of a drop (24^3 periodic, R = 6, density ratio 4, nu = 0.01, A = 1e-3) after the
     steps in which a velocity of 0.05 carries it once across the box, started at rest (U = 0) or
