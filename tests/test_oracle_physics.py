@@ -3,13 +3,16 @@
 Every test here runs the C oracle (FP64) and compares it with something the
 paper or the mathematics fixes: exact per-colour mass conservation, momentum
 balance, the BGK limit (an independent numpy transcription), the viscosity of
-Eq. (shear) from shear-wave decay, the sound speed of Eq. (press), steady
-Poiseuille flow between halfway bounce-back walls, Laplace's law with
-Eq. (sigma), the Lamb / Miller-Scriven oscillation period, the sign and
-sqrt(g) scaling of the Rayleigh-Taylor growth rate (linear theory), a
-passive colour front carried through the nozzle inlet and the convective
-outflow, and the head speed of a jet against the momentum balance at its
-stagnation point.
+Eq. (shear) from shear-wave decay, the sound speed of Eq. (press) and the bulk
+viscosity of Eq. (bulk) from a standing sound wave, steady Poiseuille flow
+between halfway bounce-back walls, Laplace's law with Eq. (sigma), the Lamb /
+Miller-Scriven oscillation period and the paper's own drop snapshots, the sign
+and sqrt(g) scaling of the Rayleigh-Taylor growth rate (linear theory) and the
+Re-independence of its fronts, a passive colour front carried through the
+nozzle inlet and the convective outflow, the head speed of a jet against the
+momentum balance at its stagnation point and its mushroom head at t* = 3, the
+Galilean invariance the Phi term of Eq. (EES) provides, and the stability
+claims of Sec. II and Sec. V.
 """
 import json
 import os
