@@ -236,10 +236,11 @@ LBM_EXPORT lbm_status lbm_macro(lbm* h, double* rhoR, double* rhoB, double* u);
 /* Diagnostics at the current time, reduced on the device in FP64 with a
  * fixed summation order (bitwise reproducible):
  *   mass_rb[2]       sum of rho_r and of rho_b over all nodes;
- *   z_leading_edge   largest z of a node with phi > 0, refined by linear
- *                    interpolation of the phi = 0 crossing towards z+1
- *                    (-1 if no node has phi > 0);
- *   dp_laplace       mean pressure over nodes with phi > 0.99 minus mean over
+ *   z_leading_edge   the jet's leading edge (Sec. IV.B): largest z of a node
+ *                    with phi > 0, refined by linear interpolation of the
+ *                    phi = 0 crossing towards z+1 (-1 if no node has phi > 0);
+ *   dp_laplace       the Laplace pressure jump of Sec. III.A (Eq. lap): mean
+ *                    pressure over nodes with phi > 0.99 minus mean over
  *                    nodes with phi < -0.99, p = sum_k rho_k 9(1-alpha_k)/19
  *                    (Eq. press); 0 if either set is empty.
  * Host pointers; any may be NULL.  Synchronises. */
