@@ -5,8 +5,9 @@ several storage precisions and reports the quantities the paper measures:
 Laplace pressure jump (Eq. lap with Eq. sigma), the n = 2 oscillation period
 (Eqs. resoFreq-Lamb), the Rayleigh-Taylor spike tip and bubble front, and the
 jet leading edge, each with its difference from the FP64 run of the same case.
-FP64 storage matches the FP64 CPU oracle to 1e-12 (tests/test_gpu_parity.py);
-where the CPU oracle can afford a case it is run too.
+FP64 storage matches the FP64 CPU oracle to 1e-12 (tests/test_gpu_parity.py), so
+the FP64 run stands for the oracle's answer; this module itself runs the CUDA
+library only.
 
     python -m paper_1705_03141_gb300.validate [--quick] [--out report.json]
 """
