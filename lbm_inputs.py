@@ -273,3 +273,11 @@ def paper_jet_cases(t_star=20.0, noise=0.01, seed=0):
                                     noise=noise, seed=seed + k, steps=int(round(t_star * D / u)),
                                     name=f"paper_jet_{name}_200x200x500_D25")
     return out
+
+
+def paper_rayleigh_taylor(Re=1024.0):
+    """The Rayleigh-Taylor runs of Sec. III.C: W = 128 (128 x 128 x 512), gravity from
+    (W g)^(1/2) = 0.04, Atwood number 0.5, equal viscosities from Re = (W g)^(1/2) W / nu (the
+    paper runs Re = 512, 1,024 and 5,120), no interfacial tension.  Time unit: sqrt(W/g) steps."""
+    W = 128
+    return rayleigh_taylor(W=W, g=0.04 ** 2 / W, Re=Re, At=0.5)

@@ -2,8 +2,9 @@
 
 Each fixture keeps the paper's numbers as printed; a value is matched to half a unit in its last
 printed digit.  Pinned here: Eq. (sigma) with tau = 3 nu + 1/2 (the sigma column of Table II), the
-lattice mapping of the jets (the lattice values of Sec. IV.B from the groups of Table III) and the
-breakup-regime labels of the batched sweep (the regimes Sec. IV.C expects for the jets of Table IV).
+lattice mapping of the jets (the lattice values of Sec. IV.B from the groups of Table III), the
+breakup-regime labels of the batched sweep (the regimes Sec. IV.C expects for the jets of Table IV)
+and the Rayleigh-Taylor set-up of Sec. III.C.
 """
 import json
 import math
@@ -126,3 +127,24 @@ def test_table_four_jets_fall_in_the_regimes_the_paper_expects():
     # Case 1 reaches its Re as the paper does: a larger jet viscosity and a slower jet
     assert works["case1"]["params"]["nu_r"] > works["ref"]["params"]["nu_r"]
     assert works["case1"]["groups"]["u_j0"] < works["ref"]["groups"]["u_j0"]
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_rayleigh_taylor_set_up_of_section_three_c(k):
+    """Sec. III.C: W x W x 4W with W = 128, (W g)^(1/2) = 0.04, At = 0.5, Re = (W g)^(1/2) W / nu for
+    Re = 512, 1,024, 5,120; heavy (red) fluid on top, no-slip top and bottom, periodic sides,
+    gravity along -z, no interfacial tension."""
+    j = _load("rayleigh_taylor_setup.json")
+    Re = float(j["Re"][k])
+    w = L.paper_rayleigh_taylor(Re)
+    p = w["params"]
+    W = printed(j["W"])[0]
+    assert w["shape"] == tuple(int(printed(v)[0]) for v in j["box"]) == (int(W), int(W), int(4 * W))
+    g = -p["g"][2]
+    assert p["g"][:2] == (0.0, 0.0) and g > 0
+    assert math.isclose(math.sqrt(W * g), float(j["sqrt_Wg"]), rel_tol=1e-12)
+    assert math.isclose((p["rho_r0"] - p["rho_b0"]) / (p["rho_r0"] + p["rho_b0"]), float(j["At"]), rel_tol=1e-12)
+    assert p["nu_r"] == p["nu_b"]
+    assert math.isclose(math.sqrt(W * g) * W / p["nu_r"], Re, rel_tol=1e-12)
+    assert p["A"] == 0.0
+    assert p["bc"][4] == p["bc"][5] == L.NOSLIP and set(p["bc"][:4]) == {L.PERIODIC}
