@@ -281,3 +281,20 @@ def paper_rayleigh_taylor(Re=1024.0):
     paper runs Re = 512, 1,024 and 5,120), no interfacial tension.  Time unit: sqrt(W/g) steps."""
     W = 128
     return rayleigh_taylor(W=W, g=0.04 ** 2 / W, Re=Re, At=0.5)
+
+
+def paper_static_droplet(R=20.0, A=1e-2):
+    """The static-droplet runs of Sec. III.A (Table I): 85^3 periodic box, red drop of radius R
+    (W = 4 profile), density ratio 1.5, viscosity ratio 1 (nu = 1e-3 for both), no gravity;
+    Table I runs R = 20, 25, 30 at A = 1e-2 and 4e-4, measured after 80,000 steps."""
+    w = static_droplet(n=85, R=R, rho_r0=1.5, rho_b0=1.0, nu_r=1e-3, nu_b=1e-3, A=A)
+    w["steps"] = 80000
+    return w
+
+
+def paper_oscillating_droplet(nu=3.333e-3, A=1e-2):
+    """The oscillating-droplet runs of Sec. III.B (Table II): 41^3 periodic box, prolate drop of
+    semi-axes 15/11/11 (W = 4 profile), density ratio 4 with the drop the dense phase
+    (rho_r0 = 1, rho_b0 = 0.25), one viscosity nu for both phases, no gravity; Table II runs
+    nu = 3.333e-3, 6.667e-3, 1.667e-2 at A = 1e-2 and 4e-4."""
+    return oscillating_droplet(n=41, axes=(15.0, 11.0, 11.0), nu=nu, A=A, rho_r0=1.0, rho_b0=0.25)

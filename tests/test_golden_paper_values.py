@@ -4,7 +4,8 @@ Each fixture keeps the paper's numbers as printed; a value is matched to half a 
 printed digit.  Pinned here: Eq. (sigma) with tau = 3 nu + 1/2 (the sigma column of Table II), the
 lattice mapping of the jets (the lattice values of Sec. IV.B from the groups of Table III), the
 breakup-regime labels of the batched sweep (the regimes Sec. IV.C expects for the jets of Table IV)
-and the Rayleigh-Taylor set-up of Sec. III.C.
+and the set-ups of the paper's own runs (Table I, Table II, Sec. III.C) as the input module builds
+them.
 """
 import json
 import math
@@ -148,3 +149,37 @@ def test_rayleigh_taylor_set_up_of_section_three_c(k):
     assert math.isclose(math.sqrt(W * g) * W / p["nu_r"], Re, rel_tol=1e-12)
     assert p["A"] == 0.0
     assert p["bc"][4] == p["bc"][5] == L.NOSLIP and set(p["bc"][:4]) == {L.PERIODIC}
+
+
+def test_static_droplet_runs_of_table_one():
+    """Sec. III.A: 85^3, W = 4, density ratio 1.5, equal viscosities 1e-3, every (R, A) of Table I,
+    periodic on all faces, no gravity, 80,000 steps."""
+    j = _load("table_one_static_drop.json")
+    st = j["setup"]
+    assert len(j["rows"]) == 6
+    for R_s, A_s, _ in j["rows"]:
+        w = L.paper_static_droplet(R=float(R_s), A=float(A_s))
+        p = w["params"]
+        n = int(printed(st["box"])[0])
+        assert w["shape"] == (n, n, n) and w["steps"] == int(st["steps"])
+        assert w["fields"] == ("sphere", {"R": float(R_s), "W": float(st["W"])})
+        assert p["rho_r0"] / p["rho_b0"] == float(st["density_ratio"])
+        assert p["nu_r"] == p["nu_b"] == float(st["nu"]) and p["nu_r"] / p["nu_b"] == float(st["viscosity_ratio"])
+        assert p["A"] == float(A_s)
+        assert set(p["bc"]) == {L.PERIODIC} and tuple(p.get("g", (0.0, 0.0, 0.0))) == (0.0, 0.0, 0.0)
+
+
+def test_oscillating_droplet_runs_of_table_two():
+    """Sec. III.B: 41^3, prolate 15/11/11, density ratio 4 (the drop the dense phase), one viscosity
+    per run, every (nu, A) of Table II, periodic, no gravity."""
+    j = _load("table_two_oscillating_drop.json")
+    st = j["setup"]
+    for nu_s, A_s, _, _ in j["rows"]:
+        w = L.paper_oscillating_droplet(nu=float(nu_s), A=float(A_s))
+        p = w["params"]
+        n = int(st["box"])
+        assert w["shape"] == (n, n, n)
+        assert w["fields"][0] == "ellipsoid" and w["fields"][1]["axes"] == tuple(float(a) for a in st["axes"])
+        assert p["rho_r0"] / p["rho_b0"] == float(st["density_ratio"])
+        assert p["nu_r"] == p["nu_b"] == float(nu_s) and p["A"] == float(A_s)
+        assert set(p["bc"]) == {L.PERIODIC} and tuple(p.get("g", (0.0, 0.0, 0.0))) == (0.0, 0.0, 0.0)
