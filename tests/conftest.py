@@ -3,6 +3,11 @@ import sys
 
 import pytest
 
+# The oracle's OpenMP threads sleep between its parallel loops instead of spinning, so that the
+# numpy work a test does between oracle steps does not compete with them for the cores (set
+# before any OpenMP runtime is loaded; an explicit setting in the environment wins).
+os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
