@@ -9,6 +9,7 @@ import itertools
 import numpy as np
 import pytest
 
+import lbm_inputs as L
 import oracle
 
 C, M, MINV, W, B, KSLOT = oracle.tables()
@@ -106,6 +107,23 @@ def test_varphi_conditions(alpha):
         assert abs((v * C[:, a]).sum()) < 1e-15
     if alpha == 8 / 27:
         np.testing.assert_allclose(v, W, atol=1e-16)  # alpha_b = 8/27 gives the plain weights
+
+
+@pytest.mark.parametrize("gamma", [1.0, 1.5, 4.0, 1000.0])
+def test_phases_at_rest_share_their_moving_populations(gamma):
+    """Eq. varphi_ik with the Grunau relation (1 - alpha_r) rho_r0 = (1 - alpha_b) rho_b0: each pure
+    phase at its reference density and at rest has the same moving populations,
+    rho_r0 varphi_i(alpha_r) = rho_b0 w_i for every i != 1, and differs from the other only in
+    its rest population (the 16-bit storages keep deviations from rho_b0 w_i for that reason).
+    Equal to rounding, which grows like gamma: 1 - alpha_r = (19/27)/gamma comes from a
+    cancellation."""
+    p = L.static_droplet(rho_r0=gamma, rho_b0=1.0)["params"]
+    ar = oracle.alpha_r(p)
+    red = oracle.equilibrium(gamma, np.zeros(3), ar)
+    blue = oracle.equilibrium(1.0, np.zeros(3), 8 / 27)
+    np.testing.assert_allclose(red[1:], blue[1:], rtol=1e-14 * gamma, atol=0)
+    np.testing.assert_allclose(blue[1:], W[1:], rtol=1e-15)
+    assert red[0] == pytest.approx(gamma * ar, rel=1e-15) and blue[0] == pytest.approx(8 / 27, rel=1e-15)
 
 
 def test_B_conditions():
