@@ -308,14 +308,12 @@ def test_suga_rates_unstable_at_tau_one():
 
 
 def _laplace(o, work):
+    """Laplace pressure jump (oracle.diagnostics, pinned on closed forms) and the equivalent
+    radius of the red volume sum (1 + phi)/2."""
     r, b, _ = o.macro()
-    p = work["params"]
-    ar, ab = oracle.alpha_r(p), 8 / 27
     phi = (r - b) / (r + b)
-    pr = r * 9 * (1 - ar) / 19 + b * 9 * (1 - ab) / 19
-    dp = pr[phi > 0.99].mean() - pr[phi < -0.99].mean()
     Req = (3 * ((1 + phi) / 2).sum() / (4 * np.pi)) ** (1 / 3)
-    return dp, Req
+    return oracle.diagnostics(r, b, work["params"])["dp"], Req
 
 
 @pytest.mark.slow
