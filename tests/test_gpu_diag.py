@@ -29,6 +29,7 @@ def test_diag_equals_the_oracle_definitions(cuda, name, storage):
     lat.step(37)
     r, b, _ = lat.macro()
     d = lat.diag()
+    assert lat.diag() == d  # fixed reduction order: bitwise the same on every call
     lat.close()
     o = oracle.diagnostics(r, b, work["params"])
     assert np.isfinite(r).all() and np.isfinite(b).all()
