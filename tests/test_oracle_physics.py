@@ -10,7 +10,8 @@ Miller-Scriven oscillation period and the paper's own drop snapshots, the sign
 and sqrt(g) scaling of the Rayleigh-Taylor growth rate (linear theory) and the
 Re-independence of its fronts, a passive colour front carried through the
 nozzle inlet and the convective outflow, the head speed of a jet against the
-momentum balance at its stagnation point and its mushroom head at t* = 3, the
+momentum balance at its stagnation point, its mushroom head at t* = 3 and the
+onset of its interface instability after t* = 9, the
 Galilean invariance the Phi term of Eq. (EES) provides, and the stability
 claims of Sec. II and Sec. V.
 """
